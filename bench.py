@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the VMC sweep of liquid 4He on GB300 (pair evaluations per second).
+
+Workload (one GPU): N = 1952 atoms at 0.02186 A^-3 (L = 44.697 A), 528 walkers, McMillan
+Jastrow b = 3.07 A, m = 5, Aziz II potential cut at L/2, uniform-cube trial step tuned to
+about 50 % acceptance, FP32 pair arithmetic with FP64 accumulators.  A step is one
+qmc_sweep call of 5 sweeps with the local energy sampled after the fifth (every row of the
+hot path: random numbers, trial moves, O(N) pair sums, decisions, housekeeping, the O(N^2)
+local energy, accumulation, write-back).  The chains are equilibrated (200 sweeps) before the
+warm-up steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun as replicas: each rank advances its own 528 walkers (disjoint
+Philox ids) with no exchange during the timed region ("weak" scaling).  The reference arm
+(--impl reference) times the FP64 CPU oracle on the host cores, on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import qmc_inputs as qi  # noqa: E402
+
+N_ATOMS, WALKERS, SWEEPS_PER_STEP = 1952, 528, 5
+METRIC = "pair evals/s and sweeps/s at N=1952, FP32-batched vs FP64 plain, E/atom within 2σ"
+WORKLOAD = "VMC liquid 4He N=1952 rho=0.02186 b=3.07 m=5 Aziz-II, 528 walkers, 5 sweeps + 1 local energy per step"
+# FP32 pipe operations per pair evaluation of the move kernel (min-image distance 9 + r^2 3,
+# u with 5th powers 11, old/new difference and accumulation 1.5 -- counted in the design doc) and per
+# directed pair of the local-energy pass.
+C_PAIR = 25.0
+C_ENERGY = 64.0
+FP32_LANES_PER_SM = 128
+
+
+def pair_evals_per_sweep(n: int) -> float:
+    return 2.0 * n * (n - 1)
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _bus_id(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def _cpu_info():
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return cores, model
+
+
+# ---------------------------------------------------------------------------------------------
+# the oracle on the host cores (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(walkers: int, nsweeps: int, step: float, seed: int = 0x5EED0003):
+    """Run the FP64 oracle on `walkers` walkers of the workload for nsweeps sweeps (local energy
+    after the last) with OpenMP over walkers.  Returns (pair evals, seconds, threads)."""
+    import oracle
+    n = N_ATOMS
+    L = qi.box_side(n, qi.RHO_HE)
+    ws = [oracle.make_walker(n, L, qi.B_HE, 5.0, step, seed=seed, wid=w, hbar2_over_m=qi.HBAR2_OVER_M)
+          for w in range(walkers)]
+    pos = [oracle.init_walker(n, L, seed, w, 0.1) for w in range(walkers)]
+    t0 = time.perf_counter()
+    _, _, _, acc, used = oracle.run_batch(ws, pos, [0.0] * walkers, [0] * walkers, nsweeps, nsweeps)
+    dt = time.perf_counter() - t0
+    return pair_evals_per_sweep(n) * nsweeps * walkers, dt, used, acc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores, model = _cpu_info()
+    walkers = cores
+    for _ in range(args.warmup):
+        oracle_sample(walkers, 1, 0.8)
+    tot_pe, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        pe, dt, used, _ = oracle_sample(walkers, 1, 0.8)
+        tot_pe += pe
+        tot_t += dt
+    value = tot_pe / tot_t
+    sample = f"{walkers} walkers x 1 sweep (+1 local energy) per step at N={N_ATOMS}, fcc start, FP64"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pair evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (OpenMP over walkers)", "cpu_model": model},
+        "cpu_baseline": {"value": value, "unit": "pair evals/s", "cores": used, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "pair evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------------------------
+def run_native(args):
+    import torch
+    import paper_1312_1282_gb300 as q
+    from paper_1312_1282_gb300 import replicas
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.cuda.current_device()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.current_stream()
+
+    n, W = N_ATOMS, WALKERS
+    L = qi.box_side(n, qi.RHO_HE)
+    pad = qi.pad4(n)
+    ids = replicas.walker_ids(rank, world, W)
+    seed = 0x5EED0003
+
+    def batch_descs(step, walkers=W, wids=ids):
+        return q.descs([(n, pad, w * 3 * pad, wids[w], L, 0.0, qi.B_HE, 5.0, step) for w in range(walkers)])
+
+    opt = q.options(precision=q.QMC_FP32, recompute_every=50)
+    pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
+    logpsi = torch.zeros(W, dtype=torch.float64, device="cuda")
+    sweeps = torch.zeros(W, dtype=torch.int64, device="cuda")
+    accum = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+    q.qmc_init_walkers(batch_descs(0.8), seed, 0.1, opt, pos)
+    q.qmc_log_psi(batch_descs(0.8), opt, pos, logpsi)
+
+    # step tuned to ~50 % acceptance: bisection on 4-sweep probes (part of equilibration)
+    lo, hi, step = 0.1, 3.0, 0.8
+    for _ in range(5):
+        d = batch_descs(step)
+        accum.zero_()
+        q.qmc_sweep(d, opt, pos, logpsi, sweeps, seed, 4, 0, accum)
+        acc_rate = accum[:, 7].sum().item() / (W * n * 4)
+        if acc_rate > 0.5:
+            lo = step
+        else:
+            hi = step
+        step = 0.5 * (lo + hi)
+    d = batch_descs(step)
+    tpw = q.qmc_autotune(d, opt, pos)
+    q.qmc_sweep(d, opt, pos, logpsi, sweeps, seed, args.equil, 0, accum)
+    accum.zero_()
+    torch.cuda.synchronize()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    def one_step():
+        q.qmc_sweep(d, opt, pos, logpsi, sweeps, seed, SWEEPS_PER_STEP, SWEEPS_PER_STEP, accum, stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    q.qmc_status(stream, 600000)
+    accum.zero_()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(_bus_id(torch, dev))
+    launches0 = q.qmc_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        one_step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clock = clocks.stop()
+    launches = q.qmc_launch_count() - launches0
+    q.qmc_status(stream, 600000)
+    times = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+        dist.barrier()
+    stats = replicas.block_stats(accum, n)
+
+    pe_step = pair_evals_per_sweep(n) * W * SWEEPS_PER_STEP
+    value = pe_step * world * args.steps / (total_ms * 1e-3)
+    sweeps_per_s = W * world * SWEEPS_PER_STEP * args.steps / (total_ms * 1e-3)
+    energy_pairs = float(n) * (n - 1) * W  # directed pairs of one local-energy pass per walker
+
+    # ---- FP64 plain single-walker path (same kernel in double, one walker) ----
+    opt64 = q.options(precision=q.QMC_FP64, recompute_every=50)
+    d1 = batch_descs(step, 1, [ids[0]])
+    pos64 = pos[:3 * pad].double().contiguous()
+    lp64, sw64, acc64 = torch.zeros(1, dtype=torch.float64, device="cuda"), torch.zeros(1, dtype=torch.int64,
+                                                                                         device="cuda"), \
+        torch.zeros(1, 8, dtype=torch.float64, device="cuda")
+    q.qmc_sweep(d1, opt64, pos64, lp64, sw64, seed, 1, 0, acc64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    q.qmc_sweep(d1, opt64, pos64, lp64, sw64, seed, 2, 0, acc64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_plain = pair_evals_per_sweep(n) * 2 / (e0.elapsed_time(e1) * 1e-3)
+
+    # ---- end to end through the public API, host buffers (pinned) ----
+    host_pos = pos.cpu().pin_memory()
+    host_lp, host_sw = logpsi.cpu().pin_memory(), sweeps.cpu().pin_memory()
+    host_acc = torch.zeros(W, 8, dtype=torch.float64).pin_memory()
+    out_pos, out_acc = torch.empty_like(host_pos).pin_memory(), torch.empty_like(host_acc).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    x0.record(stream)
+    for _ in range(e2e_steps):
+        pos.copy_(host_pos, non_blocking=True)
+        logpsi.copy_(host_lp, non_blocking=True)
+        sweeps.copy_(host_sw, non_blocking=True)
+        accum.copy_(host_acc, non_blocking=True)
+        one_step()
+        out_pos.copy_(pos, non_blocking=True)
+        out_acc.copy_(accum, non_blocking=True)
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = x0.elapsed_time(x1) / e2e_steps
+    h2d = host_pos.numel() * 4 + W * 8 * 10
+    d2h = out_pos.numel() * 4 + W * 8 * 8
+
+    # ---- roofline of the dominant kernel (the sweep kernel: one launch per step) ----
+    peaks = _peaks()
+    clk = clock.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak_tops = nsm * FP32_LANES_PER_SM * clk * 1e6 / 1e12
+    ops_launch = pe_step * C_PAIR + energy_pairs * C_ENERGY
+    achieved = ops_launch / (total_ms / args.steps * 1e-3) / 1e12
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as fh:
+            tr = json.load(fh)
+        if tr.get("kernel_hash") == _kernel_hash():
+            traffic = tr.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores, model = _cpu_info()
+        pe, dt, used, _ = oracle_sample(cores, 1, step)
+        cpu = {"value": pe / dt, "unit": "pair evals/s", "cores": used, "kind": "oracle",
+               "sample": f"{cores} walkers x 1 sweep (+1 local energy) at N={N_ATOMS}, FP64 oracle, {model}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pair evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_atoms": n, "walkers_per_gpu": W, "sweeps_per_step": SWEEPS_PER_STEP,
+                       "energy_every": SWEEPS_PER_STEP, "step_A": round(step, 4), "threads_per_walker": tpw,
+                       "sms": nsm, "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas{world}"},
+            "sweeps_per_s": sweeps_per_s,
+            "energy_pairs_per_s": energy_pairs * world * args.steps / (total_ms * 1e-3),
+            "acceptance": stats["accepted"] / (W * world * n * SWEEPS_PER_STEP * args.steps),
+            "E_per_atom": {"E": stats["E_per_atom"], "err": stats["E_err"], "V": stats["V_per_atom"],
+                           "T_L": stats["T_per_atom"], "T_PB": stats["TPB_per_atom"], "T_F": stats["TF_per_atom"],
+                           "samples_per_walker": args.steps},
+            "fp64_plain": {"value": fp64_plain, "unit": "pair evals/s", "walkers": 1,
+                           "speedup_fp32_batched": value / world / fp64_plain},
+            "e2e": {"value": pe_step * world / (e2e_ms * 1e-3), "unit": "pair evals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tops, "traffic": traffic,
+                         "note": f"FP32-pipe lane ops ({C_PAIR:g}/pair eval, {C_ENERGY:g}/energy pair) vs "
+                                 f"{nsm} SMs x 128 lanes x {clk:g} MHz",
+                         "frac_at_median_clock": (achieved / (nsm * FP32_LANES_PER_SM * clock["sm_mhz"] * 1e-6)
+                                                  if clock.get("sm_mhz") else None)},
+            "clocks": clock,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _kernel_hash():
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1312_1282_gb300", "csrc")
+    for nm in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, nm), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--equil", type=int, default=200)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

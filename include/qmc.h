@@ -1,0 +1,191 @@
+/*
+ * qmc.h -- C ABI of libqmc: variational Monte Carlo of liquid 4He on one GB300 GPU
+ * (the single-particle Metropolis sweep, its local-energy estimator and the Jastrow-parameter
+ * adjoint of Y. Lutsyshyn, "Fast quantum Monte Carlo on a GPU").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Units:       lengths in Angstrom, energies in Kelvin (totals per walker, not per atom).
+ *  Walkers:     `d` is a HOST array of W walker descriptors.  It is read during the call and
+ *               copied to a library-owned device table, cached by content, so repeated calls
+ *               with the same batch upload nothing.
+ *  Positions:   `pos` is a DEVICE buffer owned by the caller, float (QMC_FP32) or double
+ *               (QMC_FP64).  Walker w occupies pos[d[w].offset ...] as three blocks of d[w].pad_n
+ *               elements: x[pad_n] | y[pad_n] | z[pad_n] (structure of arrays).  Entries
+ *               n .. pad_n-1 of each block are ignored on input and left unchanged.  Coordinates
+ *               lie in [0, L]; the sweep keeps them there.
+ *  Outputs:     DEVICE buffers owned by the caller, double precision, W-major.
+ *  Streams:     `stream` is a cudaStream_t (NULL = legacy default stream).  Every compute call
+ *               only enqueues work on it and returns; results are ready when the stream is.
+ *  Errors:      return 0 or a negative QMC_ERR_* code; qmc_last_error() gives a message
+ *               (per host thread).  Argument and capacity errors are detected before anything
+ *               is enqueued, so no output or position is touched.  Faults found by a kernel
+ *               (a non-finite coordinate or ratio) set a device error word that qmc_status()
+ *               reads; a walker that trips it stops and writes nothing back.
+ *  Threads:     calls may come from several host threads; the descriptor cache is locked.
+ *
+ * Citations are to sections and equations of the paper.
+ */
+#ifndef QMC_H
+#define QMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QMC_VERSION 100 /* 1.0.0 */
+
+#define QMC_OK 0
+#define QMC_ERR_ARG (-1)      /* null pointer, W <= 0, n < 2, bad padding/alignment, non-finite or
+                                 out-of-range parameter */
+#define QMC_ERR_CAPACITY (-2) /* a walker does not fit one CTA's shared memory at this precision */
+#define QMC_ERR_CUDA (-3)     /* a CUDA runtime call failed (message has the CUDA error string) */
+#define QMC_ERR_DEVICE (-4)   /* a kernel flagged a non-finite coordinate or ratio (qmc_status) */
+#define QMC_ERR_TIMEOUT (-5)  /* qmc_status: the stream did not finish within the time limit */
+
+#define QMC_FP32 0 /* pair arithmetic in float, per-walker sums and ln psi in double */
+#define QMC_FP64 1 /* everything in double */
+
+#define QMC_CUBE 0  /* trial displacement uniform in the cube [-step, step]^3 */
+#define QMC_GAUSS 1 /* trial displacement Gaussian, standard deviation `step` per component */
+
+/* Device error word bits (qmc_status) */
+#define QMC_DEVERR_NONFINITE_POS 1u   /* a loaded coordinate was NaN/Inf or outside [0, L] */
+#define QMC_DEVERR_NONFINITE_RATIO 2u /* a trial log-ratio was NaN */
+#define QMC_DEVERR_BAD_INDEX 4u       /* qmc_trial_delta: an atom index outside [0, n) (move skipped) */
+
+/* One walker (one Markov chain).  64 bytes. */
+typedef struct qmc_walker_desc {
+    int32_t n;      /* number of atoms N, >= 2 */
+    int32_t pad_n;  /* block stride of pos in elements: >= n and a multiple of 4 */
+    int64_t offset; /* element offset of this walker's x block in pos: multiple of 4, >= 0 */
+    int64_t id;     /* walker id in the random-number counter (low 32 bits are used) */
+    double L;       /* cubic box side (Angstrom); <= 0 means (n / rho)^(1/3) */
+    double rho;     /* number density (Angstrom^-3), used only when L <= 0 */
+    double b;       /* Jastrow length b of Eq. (fifthPower), Angstrom, >= 0 */
+    double m_exp;   /* Jastrow exponent (5 in Eq. (fifthPower)), > 0 */
+    double step;    /* trial step: cube half-width (QMC_CUBE) or sigma (QMC_GAUSS), Angstrom */
+} qmc_walker_desc;
+
+/* Options shared by a call.  32 bytes. */
+typedef struct qmc_options {
+    int32_t precision;          /* QMC_FP32 or QMC_FP64 */
+    int32_t proposal;           /* QMC_CUBE or QMC_GAUSS */
+    int32_t sym;                /* 1: symmetrised u(r) = f(r) + f(L-r) - 2 f(L/2) (Eq. uFunction);
+                                   0: u(r) = f(r); both vanish for r >= L/2 */
+    int32_t sequential;         /* 1: move t displaces atom t; 0: atom drawn at random (Sec. 2) */
+    double hbar2_over_m;        /* hbar^2 / m_He in K Angstrom^2 (12.1194) */
+    int32_t recompute_every;    /* qmc_sweep: recompute ln psi from scratch after sweeps k with
+                                   (k+1) % recompute_every == 0; 0 = never */
+    int32_t threads_per_walker; /* 0 = autotuned choice (or built-in heuristic); else one of
+                                   32, 64, 128, 256, 512, 1024 */
+} qmc_options;
+
+/*
+ * qmc_init_walkers -- start configurations (the paper reads them from a file, Sec. 5.1).
+ * For each walker: an fcc lattice of nc^3 cubic cells with nc the smallest integer such that
+ * 4 nc^3 >= n; n of its sites picked by a Fisher-Yates shuffle driven by Philox4x32-10 stream 2;
+ * each site displaced by Gaussian noise of standard deviation jitter_sigma (Box-Muller on
+ * Philox stream 3) and wrapped into [0, L).  Key = seed; counters carry the walker id.
+ * Writes pos (entries n..pad_n-1 are set to 0).  jitter_sigma >= 0.
+ */
+int qmc_init_walkers(const qmc_walker_desc *d, int W, uint64_t seed, double jitter_sigma,
+                     const qmc_options *opt, void *pos, void *stream);
+
+/*
+ * qmc_sweep -- nsweeps Metropolis sweeps of every walker (Sec. 2, Sec. 5.1).
+ * A sweep (the paper's macroupdate, Sec. 4.1) is n single-atom moves t = 0..n-1.  Move t of sweep
+ * k draws Philox4x32-10 words with key = seed and counter (t, k, id, 0) for the displacement and
+ * dice xi, and (t/4, k, id, 1) for the atom index s (word t mod 4; s = floor(word n / 2^32)).
+ * The ratio |psi(X')|^2/|psi(X)|^2 = exp(2 Delta) with Delta of Eq. (JastrowUpdate) is compared
+ * with xi (Eq. Decision); on acceptance r_s <- wrap(r_s + delta) and logpsi += Delta.
+ * After sweep k: if recompute_every > 0 and (k+1) % recompute_every == 0, ln psi is recomputed
+ * (Eq. Jastrow); if energy_every > 0 and (k+1) % energy_every == 0, the local energy is sampled
+ * and added to accum.
+ *   pos      in/out device positions
+ *   logpsi   in/out [W] device, running ln psi (only carried, never used for decisions)
+ *   sweep    in/out [W] device, uint64 absolute sweep index k of each walker's next sweep
+ *   accum    in/out [W*8] device, added to: {sum E_L, sum E_L^2, sum V, sum T_L, sum T_PB,
+ *            sum T_F, number of samples, number of accepted moves}
+ * The same (seed, id, k) always reproduces the same chain: a run split over several calls is
+ * bit-identical to one call.
+ */
+int qmc_sweep(const qmc_walker_desc *d, int W, const qmc_options *opt, void *pos, double *logpsi,
+              uint64_t *sweep, uint64_t seed, int nsweeps, int energy_every, double *accum,
+              void *stream);
+
+/*
+ * qmc_local_energy -- local energy of each configuration (Sec. 2 Hamiltonian, Jastrow of
+ * Eqs. (Jastrow), (uFunction), (fifthPower); Aziz II potential; cutoff L/2 for V and u, Sec. 7).
+ *   out [W*5] device: {V, T_L, T_PB, T_F, E_L} with
+ *   V    = sum_{i<j, r<L/2} V(r_ij)
+ *   T_L  = -(hbar^2/2m) sum_i [nabla_i^2 ln psi + |nabla_i ln psi|^2],  E_L = V + T_L
+ *   T_PB = -(hbar^2/4m) sum_i nabla_i^2 ln psi,   T_F = (hbar^2/2m) sum_i |nabla_i ln psi|^2
+ */
+int qmc_local_energy(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos,
+                     double *out, void *stream);
+
+/*
+ * qmc_energy_grad -- ln psi, E_L and their derivatives in the Jastrow parameters (b, m) of
+ * Eq. (fifthPower), for VMC parameter optimisation (the paper has no counterpart; these are the
+ * exact derivatives of the quantities above).
+ *   out [W*6] device: {ln psi, E_L, d ln psi/db, d ln psi/dm, dE_L/db, dE_L/dm}
+ */
+int qmc_energy_grad(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos,
+                    double *out, void *stream);
+
+/*
+ * qmc_log_psi -- ln psi = sum_{i<j} u(r_ij) of each configuration (Eq. Jastrow).
+ *   out [W] device.
+ */
+int qmc_log_psi(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos,
+                double *out, void *stream);
+
+/*
+ * qmc_trial_delta -- the log-ratio Delta of Eq. (JastrowUpdate) for M trial moves per walker,
+ * each from the unchanged configuration, with the same device code as the sweep.
+ *   s     [W*M] device int32, atom index of each trial move (0 <= s < n)
+ *   delta [W*M*3] device double, displacement (dx, dy, dz) of each trial move
+ *   out   [W*M] device double, Delta of each move
+ */
+int qmc_trial_delta(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos,
+                    const int32_t *s, const double *delta, int M, double *out, void *stream);
+
+/*
+ * qmc_autotune -- time qmc_sweep on a scratch copy of `pos` for each admissible
+ * threads-per-walker choice and remember the fastest for batches of this shape (largest n,
+ * W, precision, exponent); later calls with threads_per_walker = 0 use it.  Synchronises the
+ * stream.  *tpw_out (may be NULL) receives the choice.
+ */
+int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos,
+                 void *stream, int *tpw_out);
+
+/* Largest n one walker may have at this precision (shared-memory capacity of one CTA). */
+int qmc_capacity(int precision);
+
+/*
+ * qmc_status -- wait for `stream` (at most timeout_ms, <= 0 means no limit), then read and clear
+ * the device error word.  Returns QMC_OK, QMC_ERR_DEVICE (bits in *bits if non-NULL),
+ * QMC_ERR_TIMEOUT or QMC_ERR_CUDA.
+ */
+int qmc_status(void *stream, int timeout_ms, uint32_t *bits);
+
+/* Number of kernels this library has launched since load (process-wide counter). */
+uint64_t qmc_launch_count(void);
+
+/* Message of the last error on this host thread ("" if none). */
+const char *qmc_last_error(void);
+
+/* QMC_VERSION of the loaded library. */
+int qmc_version(void);
+
+/* Free the library's device tables, autotune cache and error words. */
+void qmc_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMC_H */

@@ -1,0 +1,582 @@
+// qmc_api.cu -- host side of libqmc: the C ABI declared in include/qmc.h.
+//
+// Validates arguments, resolves walker descriptors into a device table (cached by content),
+// picks the launch shape (threads per walker from the autotuner or a heuristic, walkers per
+// CTA), and enqueues the kernels of qmc_kernels.cuh on the caller's stream.  Nothing here
+// computes physics: every step of the method runs in the kernels.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "qmc_launch.h"
+
+using namespace qmc;
+
+namespace {
+
+constexpr size_t MAX_SMEM = 232448;  // opt-in dynamic shared memory per CTA (227 KB)
+constexpr int MAX_DEVICES = 64;
+constexpr size_t MAX_PLANS = 32;
+
+thread_local std::string g_err;
+std::atomic<unsigned long long> g_launches{0};
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(QMC_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+struct DeviceState {
+    unsigned *err = nullptr;
+    int nsm = 0;
+};
+
+std::mutex g_mu;
+DeviceState g_dev[MAX_DEVICES];
+
+struct Plan {
+    int device = 0;
+    uint64_t key = 0;
+    std::vector<qmc_walker_desc> descs;
+    int sym = 1;
+    int W = 0;
+    DevWalker *d_walkers = nullptr;
+    int *d_order = nullptr;
+    int maxn = 0, maxpad = 0, maxsites = 0;
+    bool m5 = true;
+};
+
+std::list<Plan *> g_plans;                 // most recently used first
+std::unordered_map<uint64_t, int> g_tuned;  // shape key -> threads per walker
+
+uint64_t fnv(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+int current_device(int &dev)
+{
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(QMC_ERR_CUDA, "device ordinal %d out of range", dev);
+    return QMC_OK;
+}
+
+// Per-device error word and SM count, created on first use (not capturable: make the first
+// call of a process outside stream capture).
+int device_state(int dev, DeviceState *&ds)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    ds = &g_dev[dev];
+    if (ds->err) return QMC_OK;
+    cudaError_t e = cudaDeviceGetAttribute(&ds->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    unsigned *p = nullptr;
+    e = cudaMalloc(&p, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(error word)");
+    e = cudaMemset(p, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(error word)");
+    ds->err = p;
+    return QMC_OK;
+}
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+int check_options(const qmc_options *o)
+{
+    if (!o) return fail(QMC_ERR_ARG, "options pointer is NULL");
+    if (o->precision != QMC_FP32 && o->precision != QMC_FP64)
+        return fail(QMC_ERR_ARG, "precision must be QMC_FP32 or QMC_FP64");
+    if (o->proposal != QMC_CUBE && o->proposal != QMC_GAUSS)
+        return fail(QMC_ERR_ARG, "proposal must be QMC_CUBE or QMC_GAUSS");
+    if (o->sym != 0 && o->sym != 1) return fail(QMC_ERR_ARG, "sym must be 0 or 1");
+    if (o->sequential != 0 && o->sequential != 1) return fail(QMC_ERR_ARG, "sequential must be 0 or 1");
+    if (!is_fin(o->hbar2_over_m) || o->hbar2_over_m <= 0) return fail(QMC_ERR_ARG, "hbar2_over_m must be > 0");
+    if (o->recompute_every < 0) return fail(QMC_ERR_ARG, "recompute_every must be >= 0");
+    const int t = o->threads_per_walker;
+    if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256 && t != 512 && t != 1024)
+        return fail(QMC_ERR_ARG, "threads_per_walker must be 0 or a power of two in 32..1024");
+    return QMC_OK;
+}
+
+size_t elem_size(int precision) { return precision == QMC_FP64 ? sizeof(double) : sizeof(float); }
+
+size_t smem_group(int precision, int stride, int tpw)
+{
+    return precision == QMC_FP64 ? group_smem<double>(stride, tpw) : group_smem<float>(stride, tpw);
+}
+
+int sites_of(int n)
+{
+    int nc = 1;
+    while (4LL * nc * nc * nc < n) ++nc;
+    return 4 * nc * nc * nc;
+}
+
+// Validate and resolve descriptors (host copy of the device table).
+int resolve(const qmc_walker_desc *d, int W, const qmc_options *o, Plan &P, std::vector<DevWalker> &out,
+            std::vector<int> &order)
+{
+    out.resize(W);
+    P.maxn = P.maxpad = P.maxsites = 0;
+    P.m5 = true;
+    for (int w = 0; w < W; ++w) {
+        const qmc_walker_desc &x = d[w];
+        if (x.n < 2) return fail(QMC_ERR_ARG, "walker %d: n = %d < 2", w, x.n);
+        if (x.pad_n < x.n || x.pad_n % 4) return fail(QMC_ERR_ARG, "walker %d: pad_n must be >= n and a multiple of 4", w);
+        if (x.offset < 0 || x.offset % 4) return fail(QMC_ERR_ARG, "walker %d: offset must be >= 0 and a multiple of 4", w);
+        double L = x.L;
+        if (!(L > 0)) {
+            if (!is_fin(x.rho) || x.rho <= 0) return fail(QMC_ERR_ARG, "walker %d: need L > 0 or rho > 0", w);
+            L = std::cbrt((double)x.n / x.rho);
+        }
+        if (!is_fin(L)) return fail(QMC_ERR_ARG, "walker %d: non-finite box side", w);
+        if (!is_fin(x.b) || x.b < 0) return fail(QMC_ERR_ARG, "walker %d: b must be finite and >= 0", w);
+        if (!is_fin(x.m_exp) || x.m_exp <= 0) return fail(QMC_ERR_ARG, "walker %d: m_exp must be finite and > 0", w);
+        if (!is_fin(x.step) || x.step <= 0) return fail(QMC_ERR_ARG, "walker %d: step must be finite and > 0", w);
+        // a displacement must stay below one box length so one fold puts it back into the box
+        const double reach = o->proposal == QMC_CUBE ? x.step : 6.8 * x.step;
+        if (reach >= L) return fail(QMC_ERR_ARG, "walker %d: step too large for box side %g", w, L);
+        DevWalker &v = out[w];
+        v.n = x.n;
+        v.pad = x.pad_n;
+        v.off = x.offset;
+        v.wid = (uint32_t)x.id;
+        v.slot = w;
+        v.L = L;
+        v.b = x.b;
+        v.m = x.m_exp;
+        v.step = x.step;
+        v.c = -0.5 * std::pow(x.b, x.m_exp);
+        v.K = o->sym ? 2.0 * v.c * std::pow(2.0 / L, x.m_exp) : 0.0;
+        P.maxn = std::max(P.maxn, x.n);
+        P.maxpad = std::max(P.maxpad, x.pad_n);
+        P.maxsites = std::max(P.maxsites, sites_of(x.n));
+        if (x.m_exp != 5.0) P.m5 = false;
+    }
+    order.resize(W);
+    for (int w = 0; w < W; ++w) order[w] = w;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d[a].n > d[b].n; });
+    return QMC_OK;
+}
+
+void free_plan(Plan *p)
+{
+    if (p->d_walkers) cudaFree(p->d_walkers);
+    if (p->d_order) cudaFree(p->d_order);
+    delete p;
+}
+
+// Find or build the device table of a batch.
+int get_plan(const qmc_walker_desc *d, int W, const qmc_options *o, cudaStream_t st, Plan *&out)
+{
+    if (!d) return fail(QMC_ERR_ARG, "descriptor pointer is NULL");
+    if (W <= 0) return fail(QMC_ERR_ARG, "W must be > 0");
+    int dev;
+    int rc = current_device(dev);
+    if (rc) return rc;
+    const int sym = o->sym;
+    uint64_t key = fnv(d, sizeof(qmc_walker_desc) * (size_t)W);
+    key = fnv(&W, sizeof W, key);
+    key = fnv(&dev, sizeof dev, key);
+    key = fnv(&sym, sizeof sym, key);
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
+        Plan *p = *it;
+        if (p->key == key && p->W == W && p->device == dev && p->sym == sym &&
+            std::memcmp(p->descs.data(), d, sizeof(qmc_walker_desc) * (size_t)W) == 0) {
+            g_plans.splice(g_plans.begin(), g_plans, it);
+            out = p;
+            return QMC_OK;
+        }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(QMC_ERR_ARG, "a new walker batch cannot be registered during stream capture; "
+                                 "call once with this batch before capturing");
+    Plan *p = new Plan;
+    p->device = dev;
+    p->key = key;
+    p->W = W;
+    p->sym = sym;
+    p->descs.assign(d, d + W);
+    std::vector<DevWalker> host;
+    std::vector<int> order;
+    rc = resolve(d, W, o, *p, host, order);
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    cudaError_t e = cudaMalloc(&p->d_walkers, sizeof(DevWalker) * (size_t)W);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int) * (size_t)W);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_walkers, host.data(), sizeof(DevWalker) * (size_t)W, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_order, order.data(), sizeof(int) * (size_t)W, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "walker table upload");
+    }
+    g_plans.push_front(p);
+    while (g_plans.size() > MAX_PLANS) {
+        free_plan(g_plans.back());
+        g_plans.pop_back();
+    }
+    out = p;
+    return QMC_OK;
+}
+
+Variant variant_of(const Plan &P, const qmc_options *o) { return o->sym ? (P.m5 ? V5S : VGS) : VGN; }
+
+uint64_t shape_key(int dev, const Plan &P, const qmc_options *o)
+{
+    int v[6] = {dev, o->precision, (int)variant_of(P, o), P.maxn, P.W, o->proposal};
+    return fnv(v, sizeof v);
+}
+
+int pow2_at_least(int x)
+{
+    int p = 32;
+    while (p < x && p < 1024) p <<= 1;
+    return p;
+}
+
+// Threads per walker: explicit option, then the autotuned choice, then a heuristic aiming at
+// ~16 resident warps per SM while every thread keeps at least one 4-atom partner chunk.
+int choose_tpw(const Plan &P, const qmc_options *o, int dev, int nsm)
+{
+    if (o->threads_per_walker) return o->threads_per_walker;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_tuned.find(shape_key(dev, P, o));
+        if (it != g_tuned.end()) return it->second;
+    }
+    const int chunks = (P.maxn + 3) / 4;
+    int t = pow2_at_least((int)std::ceil(512.0 * nsm / P.W));
+    t = std::min(t, pow2_at_least(chunks));
+    return std::max(32, std::min(t, 1024));
+}
+
+// Walkers per CTA: one, unless the batch has so many small walkers that the 32-CTA-per-SM
+// limit would cap residency.
+int choose_groups(const Plan &P, int precision, int tpw, int nsm)
+{
+    int G = 1;
+    if (tpw <= 128 && P.W > 24 * nsm) G = std::min(256 / tpw, (P.W + 24 * nsm - 1) / (24 * nsm));
+    while (G > 1 && (size_t)G * smem_group(precision, P.maxpad, tpw) > MAX_SMEM) --G;
+    return std::max(1, std::min(G, 8));
+}
+
+int check_capacity(const Plan &P, int precision, int tpw)
+{
+    if (smem_group(precision, P.maxpad, tpw) > MAX_SMEM)
+        return fail(QMC_ERR_CAPACITY, "a walker with pad_n = %d does not fit shared memory at %s (max n %d)",
+                    P.maxpad, precision == QMC_FP64 ? "FP64" : "FP32", qmc_capacity(precision));
+    return QMC_OK;
+}
+
+int check_ptr(const void *p, const char *name, size_t align)
+{
+    if (!p) return fail(QMC_ERR_ARG, "%s is NULL", name);
+    if ((uintptr_t)p % align) return fail(QMC_ERR_ARG, "%s must be %zu-byte aligned", name, align);
+    return QMC_OK;
+}
+
+cudaError_t launch_sweep(int precision, int tpw, Variant v, int grid, int block, size_t smem, cudaStream_t st,
+                         const SweepArgs &a)
+{
+    if (precision == QMC_FP64)
+        return tpw <= 128 ? launch_sweep_f64_small(tpw, v, grid, block, smem, st, a)
+                          : launch_sweep_f64_big(tpw, v, grid, block, smem, st, a);
+    return tpw <= 128 ? launch_sweep_f32_small(tpw, v, grid, block, smem, st, a)
+                      : launch_sweep_f32_big(tpw, v, grid, block, smem, st, a);
+}
+
+struct Prep {
+    Plan *plan = nullptr;
+    DeviceState *ds = nullptr;
+    int dev = 0;
+};
+
+// Host-only checks come first, so argument errors are reported without touching the device.
+int prepare(const qmc_walker_desc *d, int W, const qmc_options *o, cudaStream_t st, Prep &p)
+{
+    int rc = check_options(o);
+    if (rc) return rc;
+    if (!d) return fail(QMC_ERR_ARG, "descriptor pointer is NULL");
+    if (W <= 0) return fail(QMC_ERR_ARG, "W must be > 0");
+    if ((rc = current_device(p.dev))) return rc;
+    if ((rc = device_state(p.dev, p.ds))) return rc;
+    return get_plan(d, W, o, st, p.plan);
+}
+
+int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos, double *logpsi, uint64_t *sweep,
+               uint64_t seed, int nsweeps, int energy_every, double *accum, cudaStream_t st, int tpw_force)
+{
+    int rc;
+    if ((rc = check_ptr(pos, "pos", 16)) || (rc = check_ptr(logpsi, "logpsi", 8)) ||
+        (rc = check_ptr(sweep, "sweep", 8)) || (rc = check_ptr(accum, "accum", 8)))
+        return rc;
+    if (nsweeps < 0) return fail(QMC_ERR_ARG, "nsweeps must be >= 0");
+    if (energy_every < 0) return fail(QMC_ERR_ARG, "energy_every must be >= 0");
+    Prep p;
+    if ((rc = prepare(d, W, o, st, p))) return rc;
+    const Plan &P = *p.plan;
+    const int tpw = tpw_force ? tpw_force : choose_tpw(P, o, p.dev, p.ds->nsm);
+    if ((rc = check_capacity(P, o->precision, tpw))) return rc;
+    if (nsweeps == 0) return QMC_OK;
+    const int G = choose_groups(P, o->precision, tpw, p.ds->nsm);
+    SweepArgs a;
+    a.walkers = P.d_walkers;
+    a.order = P.d_order;
+    a.W = W;
+    a.G = G;
+    a.stride = P.maxpad;
+    a.pos = pos;
+    a.logpsi = logpsi;
+    a.sweep = reinterpret_cast<unsigned long long *>(sweep);
+    a.accum = accum;
+    a.seed = seed;
+    a.nsweeps = nsweeps;
+    a.energy_every = energy_every;
+    a.recompute_every = o->recompute_every;
+    a.proposal = o->proposal;
+    a.sequential = o->sequential;
+    a.h2m = o->hbar2_over_m;
+    a.err = p.ds->err;
+    const int grid = (W + G - 1) / G;
+    const size_t smem = (size_t)G * smem_group(o->precision, P.maxpad, tpw);
+    cudaError_t e = launch_sweep(o->precision, tpw, variant_of(P, o), grid, G * tpw, smem, st, a);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+    g_launches.fetch_add(1);
+    return QMC_OK;
+}
+
+int pass_impl(const qmc_walker_desc *d, int W, const qmc_options *o, const void *pos, double *out, int kind,
+              const int32_t *s, const double *delta, int M, cudaStream_t st)
+{
+    int rc;
+    if ((rc = check_ptr(pos, "pos", 16)) || (rc = check_ptr(out, "out", 8))) return rc;
+    Prep p;
+    if ((rc = prepare(d, W, o, st, p))) return rc;
+    const Plan &P = *p.plan;
+    const int tpw = kind == 2 ? TRIAL_TPW : PASS_TPW;
+    if ((rc = check_capacity(P, o->precision, tpw))) return rc;
+    PassArgs a;
+    a.walkers = P.d_walkers;
+    a.W = W;
+    a.stride = P.maxpad;
+    a.pos = pos;
+    a.out = out;
+    a.h2m = o->hbar2_over_m;
+    a.s = s;
+    a.delta = delta;
+    a.M = M;
+    a.err = p.ds->err;
+    const size_t smem = smem_group(o->precision, P.maxpad, tpw);
+    cudaError_t e = launch_pass(o->precision, variant_of(P, o), kind, W, smem, st, a);
+    if (e != cudaSuccess) return cuda_fail(e, "pass launch");
+    g_launches.fetch_add(1);
+    return QMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qmc_init_walkers(const qmc_walker_desc *d, int W, uint64_t seed, double jitter_sigma, const qmc_options *opt,
+                     void *pos, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if ((rc = check_ptr(pos, "pos", 16))) return rc;
+    if (!is_fin(jitter_sigma) || jitter_sigma < 0) return fail(QMC_ERR_ARG, "jitter_sigma must be finite and >= 0");
+    Prep p;
+    if ((rc = prepare(d, W, opt, st, p))) return rc;
+    const size_t smem = sizeof(int) * (size_t)p.plan->maxsites;
+    if (smem > MAX_SMEM) return fail(QMC_ERR_CAPACITY, "too many lattice sites for the start configuration");
+    cudaError_t e = launch_init(opt->precision, W, smem, st, p.plan->d_walkers, seed, jitter_sigma, pos);
+    if (e != cudaSuccess) return cuda_fail(e, "init launch");
+    g_launches.fetch_add(1);
+    return QMC_OK;
+}
+
+int qmc_sweep(const qmc_walker_desc *d, int W, const qmc_options *opt, void *pos, double *logpsi, uint64_t *sweep,
+              uint64_t seed, int nsweeps, int energy_every, double *accum, void *stream)
+{
+    return sweep_impl(d, W, opt, pos, logpsi, sweep, seed, nsweeps, energy_every, accum, (cudaStream_t)stream, 0);
+}
+
+int qmc_local_energy(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos, double *out,
+                     void *stream)
+{
+    return pass_impl(d, W, opt, pos, out, 0, nullptr, nullptr, 0, (cudaStream_t)stream);
+}
+
+int qmc_log_psi(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos, double *out, void *stream)
+{
+    return pass_impl(d, W, opt, pos, out, 1, nullptr, nullptr, 0, (cudaStream_t)stream);
+}
+
+int qmc_trial_delta(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos, const int32_t *s,
+                    const double *delta, int M, double *out, void *stream)
+{
+    if (M <= 0) return fail(QMC_ERR_ARG, "M must be > 0");
+    if (!s || !delta) return fail(QMC_ERR_ARG, "s and delta must not be NULL");
+    return pass_impl(d, W, opt, pos, out, 2, s, delta, M, (cudaStream_t)stream);
+}
+
+int qmc_energy_grad(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos, double *out,
+                    void *stream)
+{
+    return pass_impl(d, W, opt, pos, out, 3, nullptr, nullptr, 0, (cudaStream_t)stream);
+}
+
+int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos, void *stream,
+                 int *tpw_out)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if ((rc = check_ptr(pos, "pos", 16))) return rc;
+    Prep p;
+    if ((rc = prepare(d, W, opt, st, p))) return rc;
+    const Plan &P = *p.plan;
+    size_t elems = 0;
+    for (int w = 0; w < W; ++w) elems = std::max(elems, (size_t)(d[w].offset + 3 * (int64_t)d[w].pad_n));
+    const size_t bytes = elems * elem_size(opt->precision);
+    void *scratch = nullptr;
+    double *lp = nullptr, *acc = nullptr;
+    uint64_t *sw = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int best = 0;
+    float best_ms = 0;
+    cudaError_t e = cudaMalloc(&scratch, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&lp, sizeof(double) * W);
+    if (e == cudaSuccess) e = cudaMalloc(&acc, sizeof(double) * 8 * W);
+    if (e == cudaSuccess) e = cudaMalloc(&sw, sizeof(uint64_t) * W);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lp, 0, sizeof(double) * W, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(double) * 8 * W, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sw, 0, sizeof(uint64_t) * W, st);
+    const int chunk_cap = pow2_at_least((P.maxn + 3) / 4);
+    for (int tpw = 32; e == cudaSuccess && tpw <= 1024; tpw <<= 1) {
+        if (tpw > chunk_cap) break;
+        if (smem_group(opt->precision, P.maxpad, tpw) > MAX_SMEM) continue;
+        e = cudaMemcpyAsync(scratch, pos, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) break;
+        rc = sweep_impl(d, W, opt, scratch, lp, sw, 0x7E57ull, 1, 0, acc, st, tpw);  // warm-up
+        if (rc) break;
+        e = cudaEventRecord(e0, st);
+        if (e != cudaSuccess) break;
+        rc = sweep_impl(d, W, opt, scratch, lp, sw, 0x7E57ull, 2, 0, acc, st, tpw);
+        if (rc) break;
+        e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
+            best = tpw;
+            best_ms = ms;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(scratch);
+    cudaFree(lp);
+    cudaFree(acc);
+    cudaFree(sw);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    if (best == 0) return fail(QMC_ERR_CAPACITY, "no admissible threads-per-walker choice");
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_tuned[shape_key(p.dev, P, opt)] = best;
+    }
+    if (tpw_out) *tpw_out = best;
+    return QMC_OK;
+}
+
+int qmc_capacity(int precision)
+{
+    if (precision != QMC_FP32 && precision != QMC_FP64) return fail(QMC_ERR_ARG, "bad precision");
+    const size_t es = elem_size(precision);
+    const size_t red = smem_group(precision, 0, 1024);
+    return (int)(((MAX_SMEM - red) / (3 * es)) / 4 * 4);
+}
+
+int qmc_status(void *stream, int timeout_ms, uint32_t *bits)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev;
+    int rc = current_device(dev);
+    if (rc) return rc;
+    DeviceState *ds;
+    if ((rc = device_state(dev, ds))) return rc;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(st);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_fail(q, "cudaStreamQuery");
+        if (timeout_ms > 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+            return fail(QMC_ERR_TIMEOUT, "stream not finished after %d ms", timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    unsigned h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, ds->err, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ds->err, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    if (bits) *bits = h;
+    if (h)
+        return fail(QMC_ERR_DEVICE, "kernel flagged %s%s%s", (h & QMC_DEVERR_NONFINITE_POS) ? "[bad coordinate]" : "",
+                    (h & QMC_DEVERR_NONFINITE_RATIO) ? "[non-finite ratio]" : "",
+                    (h & QMC_DEVERR_BAD_INDEX) ? "[atom index out of range]" : "");
+    return QMC_OK;
+}
+
+uint64_t qmc_launch_count(void) { return g_launches.load(); }
+
+const char *qmc_last_error(void) { return g_err.c_str(); }
+
+int qmc_version(void) { return QMC_VERSION; }
+
+void qmc_shutdown(void)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (Plan *p : g_plans) free_plan(p);
+    g_plans.clear();
+    g_tuned.clear();
+    for (auto &ds : g_dev) {
+        if (ds.err) cudaFree(ds.err);
+        ds.err = nullptr;
+        ds.nsm = 0;
+    }
+}
+
+}  // extern "C"

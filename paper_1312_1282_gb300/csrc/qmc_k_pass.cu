@@ -1,0 +1,88 @@
+// Stand-alone passes (local energy, ln psi, trial ratios, (b, m) gradient) and the start
+// configuration kernel, both precisions.
+#include "qmc_launch.h"
+
+namespace qmc {
+
+template <typename K> static cudaError_t big_smem(K k)
+{
+    static_assert(sizeof(K) > 0, "");
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess) cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
+template <typename T, int MEXP, bool SYM>
+static cudaError_t pass_go(int kind, int grid, size_t smem, cudaStream_t st, const PassArgs &a)
+{
+    if (kind == 0 || kind == 1) {
+        auto k = pass_kernel<T, MEXP, SYM, PASS_TPW>;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = big_smem(k);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k<<<grid, PASS_TPW, smem, st>>>(a, kind);
+    } else if (kind == 2) {
+        auto k = trial_kernel<T, MEXP, SYM, TRIAL_TPW>;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = big_smem(k);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k<<<grid, TRIAL_TPW, smem, st>>>(a);
+    } else {
+        auto k = grad_kernel<T, SYM, PASS_TPW>;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = big_smem(k);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k<<<grid, PASS_TPW, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t pass_t(Variant v, int kind, int grid, size_t smem, cudaStream_t st, const PassArgs &a)
+{
+    switch (v) {
+    case V5S: return pass_go<T, 5, true>(kind, grid, smem, st, a);
+    case VGS: return pass_go<T, 0, true>(kind, grid, smem, st, a);
+    default: return pass_go<T, 0, false>(kind, grid, smem, st, a);
+    }
+}
+
+cudaError_t launch_pass(int precision, Variant v, int kind, int grid, size_t smem, cudaStream_t st, const PassArgs &a)
+{
+    return precision == QMC_FP64 ? pass_t<double>(v, kind, grid, smem, st, a)
+                                 : pass_t<float>(v, kind, grid, smem, st, a);
+}
+
+cudaError_t launch_init(int precision, int grid, size_t smem, cudaStream_t st, const DevWalker *walkers,
+                        unsigned long long seed, double sigma, void *pos)
+{
+    if (precision == QMC_FP64) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = big_smem(init_kernel<double>);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        init_kernel<double><<<grid, 256, smem, st>>>(walkers, seed, sigma, pos);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = big_smem(init_kernel<float>);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        init_kernel<float><<<grid, 256, smem, st>>>(walkers, seed, sigma, pos);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace qmc

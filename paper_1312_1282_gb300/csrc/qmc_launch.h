@@ -1,0 +1,34 @@
+// qmc_launch.h -- internal interface between the host API (qmc_api.cu) and the kernel
+// translation units (qmc_k_*.cu), which instantiate the templates of qmc_kernels.cuh.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qmc_kernels.cuh"
+
+namespace qmc {
+
+// Jastrow variants compiled: 5 = exponent 5 by multiplication, symmetrised u;
+// GS = general exponent, symmetrised; GN = general exponent, plain truncated u.
+enum Variant { V5S = 0, VGS = 1, VGN = 2 };
+
+// Each launcher returns the launch error (cudaSuccess if enqueued).
+cudaError_t launch_sweep_f32_small(int tpw, Variant v, int grid, int block, size_t smem, cudaStream_t st,
+                                   const SweepArgs &a);  // tpw 32, 64, 128
+cudaError_t launch_sweep_f32_big(int tpw, Variant v, int grid, int block, size_t smem, cudaStream_t st,
+                                 const SweepArgs &a);  // tpw 256, 512, 1024
+cudaError_t launch_sweep_f64_small(int tpw, Variant v, int grid, int block, size_t smem, cudaStream_t st,
+                                   const SweepArgs &a);
+cudaError_t launch_sweep_f64_big(int tpw, Variant v, int grid, int block, size_t smem, cudaStream_t st,
+                                 const SweepArgs &a);
+
+constexpr int PASS_TPW = 256;   // threads per walker of the stand-alone passes
+constexpr int TRIAL_TPW = 128;  // threads per walker of qmc_trial_delta
+
+// kind 0: local energy, 1: ln psi, 2: trial deltas, 3: energy + (b, m) gradient
+cudaError_t launch_pass(int precision, Variant v, int kind, int grid, size_t smem, cudaStream_t st,
+                        const PassArgs &a);
+cudaError_t launch_init(int precision, int grid, size_t smem, cudaStream_t st, const DevWalker *walkers,
+                        unsigned long long seed, double sigma, void *pos);
+
+}  // namespace qmc

@@ -1,0 +1,160 @@
+"""GPU vs oracle on fixed configurations: local energy, ln psi, (b, m) gradient, trial ratios
+and start configurations, through the C ABI.  FP64: 1e-10 relative; FP32: 1e-5 relative
+(the tolerances of the method's fixed-configuration parity), on batches whose sizes span
+several partner chunks and thread groups with ragged tails."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1312_1282_gb300 as q
+import qmc_inputs as qi
+from tests._gpu import H2M, Packed, lattice_batch, zeros
+
+pytestmark = pytest.mark.gpu
+
+NS = [2, 3, 5, 17, 64, 130, 257, 512, 1001]
+TOL = {q.QMC_FP64: 1e-10, q.QMC_FP32: 1e-5}
+PREC = [q.QMC_FP64, q.QMC_FP32]
+
+
+def _close(got, want, rel, scale=None):
+    scale = np.maximum(np.abs(want), 1e-300) if scale is None else scale
+    err = np.abs(np.asarray(got) - np.asarray(want)) / scale
+    assert np.all(err <= rel), (err.max(), got, want)
+
+
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("sym,m", [(1, 5.0), (1, 4.6), (0, 5.0)])
+def test_local_energy(prec, sym, m):
+    P = lattice_batch(NS, prec, seed=10, ms=m)
+    opt = q.options(precision=prec, sym=sym)
+    out = zeros((P.W, 5))
+    q.qmc_local_energy(P.d, opt, P.pos, out)
+    got = out.cpu().numpy()
+    for w in range(P.W):
+        want = oracle.local_energy(P.confs[w], P.Ls[w], P.bs[w], m, sym, H2M)
+        # E_L = V + T_L is compared on the scale of the two terms it is built from
+        scale = np.abs(want).copy()
+        scale[4] = abs(want[0]) + abs(want[1])
+        _close(got[w], want, TOL[prec], np.maximum(scale, 1e-12))
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_log_psi(prec):
+    P = lattice_batch(NS, prec, seed=20)
+    out = zeros(P.W)
+    q.qmc_log_psi(P.d, q.options(precision=prec), P.pos, out)
+    want = [oracle.log_psi(P.confs[w], P.Ls[w], P.bs[w]) for w in range(P.W)]
+    _close(out.cpu().numpy(), want, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_energy_grad(prec):
+    ns = [2, 17, 64, 130, 512]
+    P = lattice_batch(ns, prec, seed=30, bs=[2.95, 3.0, 3.07, 3.1, 3.2])
+    out = zeros((P.W, 6))
+    q.qmc_energy_grad(P.d, q.options(precision=prec), P.pos, out)
+    got = out.cpu().numpy()
+    for w in range(P.W):
+        want = oracle.energy_grad(P.confs[w], P.Ls[w], P.bs[w], 5.0, 1, H2M)
+        e = oracle.local_energy(P.confs[w], P.Ls[w], P.bs[w], 5.0, 1, H2M)
+        lap, F = oracle.local_terms(P.confs[w], P.Ls[w], P.bs[w])
+        # derivatives of E_L are sums of kinetic terms with both signs: their scale is the
+        # kinetic magnitude times the derivative's own factor
+        kin = 0.5 * H2M * (np.abs(lap).sum() + (F ** 2).sum())
+        scale = np.array([abs(want[0]), abs(e[0]) + abs(e[1]), abs(want[2]), abs(want[3]) + 1e-300,
+                          kin * 5.0 / P.bs[w] * 2, kin * 4.0])
+        tol = TOL[prec] * (20 if prec == q.QMC_FP32 else 1)
+        _close(got[w], want, tol, np.maximum(scale, 1e-12))
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_trial_delta(prec):
+    ns = [3, 17, 64, 130, 512, 1001]
+    P = lattice_batch(ns, prec, seed=40)
+    M = 24
+    rng = np.random.default_rng(5)
+    s = np.stack([rng.integers(0, n, size=M) for n in ns]).astype(np.int32)
+    delta = rng.uniform(-1.5, 1.5, size=(P.W, M, 3))
+    out = zeros((P.W, M))
+    q.qmc_trial_delta(P.d, q.options(precision=prec), P.pos, torch.tensor(s, device="cuda"),
+                      torch.tensor(delta, device="cuda"), M, out)
+    got = out.cpu().numpy()
+    for w in range(P.W):
+        lp = oracle.log_psi(P.confs[w], P.Ls[w], P.bs[w])
+        row = 4 * abs(lp) / ns[w] + 1e-3  # typical sum_j |u| of one atom, old + new
+        for k in range(M):
+            d = delta[w, k]
+            if prec == q.QMC_FP32:
+                d = d.astype(np.float32).astype(np.float64)
+            want, _ = oracle.trial_delta(P.confs[w], P.Ls[w], P.bs[w], 5.0, 1, s[w, k], d)
+            assert abs(got[w, k] - want) <= TOL[prec] * row * 10, (w, k, got[w, k], want, row)
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_init_walkers_match_oracle(prec):
+    ns = [2, 64, 130, 500, 1952]
+    rows, off = [], 0
+    for i, n in enumerate(ns):
+        pad = qi.pad4(n)
+        rows.append((n, pad, off, 7 + i, 0.0, qi.RHO_HE, 3.07, 5.0, 0.8))
+        off += 3 * pad
+    d = q.descs(rows)
+    dt = torch.float64 if prec == q.QMC_FP64 else torch.float32
+    pos = torch.full((off,), -1.0, dtype=dt, device="cuda")
+    q.qmc_init_walkers(d, 0x5EED0002, 0.1, q.options(precision=prec), pos)
+    host = pos.cpu().numpy().astype(np.float64)
+    for i, n in enumerate(ns):
+        L = (n / qi.RHO_HE) ** (1 / 3)
+        r = rows[i]
+        blk = host[r[2]:r[2] + 3 * r[1]].reshape(3, r[1])
+        want = oracle.init_walker(n, L, 0x5EED0002, 7 + i, 0.1)
+        atol = 1e-12 * L if prec == q.QMC_FP64 else 2 * np.spacing(np.float32(L))
+        assert np.allclose(blk[:, :n], want, rtol=0, atol=atol)
+        assert np.all(blk[:, n:] == 0.0)
+
+
+def test_padding_is_ignored_and_left_alone():
+    P = lattice_batch([5, 130], q.QMC_FP32, seed=50, junk=float("nan"))
+    out = zeros((P.W, 5))
+    q.qmc_local_energy(P.d, q.options(), P.pos, out)
+    assert torch.isfinite(out).all()
+    lp, sw, acc = zeros(P.W), zeros(P.W, torch.int64), zeros((P.W, 8))
+    q.qmc_sweep(P.d, q.options(), P.pos, lp, sw, 1, 2, 1, acc)
+    assert q.qmc_status(timeout_ms=60000) == 0
+    assert np.all(np.isnan(P.padding(0))) and np.all(np.isnan(P.padding(1)))
+
+
+def test_capacity_and_argument_errors():
+    big = lattice_batch([2], q.QMC_FP32)
+    rows = [(q.qmc_capacity(q.QMC_FP32) + 8, q.qmc_capacity(q.QMC_FP32) + 8, 0, 0, 100.0, 0, 3.07, 5.0, 0.8)]
+    with pytest.raises(q.QmcError, match="CAPACITY"):
+        q.qmc_local_energy(q.descs(rows), q.options(), big.pos, zeros(5))
+    rows = [(10000, 10000, 0, 0, 77.0, 0, 3.07, 5.0, 0.8)]
+    with pytest.raises(q.QmcError, match="CAPACITY"):
+        q.qmc_local_energy(q.descs(rows), q.options(precision=q.QMC_FP64), big.pos, zeros(5))
+    for bad in [(1, 4, 0, 0, 10.0, 0, 3.0, 5.0, 0.8), (8, 6, 0, 0, 10.0, 0, 3.0, 5.0, 0.8),
+                (8, 8, 2, 0, 10.0, 0, 3.0, 5.0, 0.8), (8, 8, 0, 0, 0.0, 0.0, 3.0, 5.0, 0.8),
+                (8, 8, 0, 0, 10.0, 0, -1.0, 5.0, 0.8), (8, 8, 0, 0, 10.0, 0, 3.0, 5.0, 11.0),
+                (8, 8, 0, 0, 10.0, 0, math.nan, 5.0, 0.8)]:
+        with pytest.raises(q.QmcError, match="ARG"):
+            q.qmc_local_energy(q.descs([bad]), q.options(), big.pos, zeros(5))
+
+
+def test_nonfinite_coordinates_are_flagged_not_faulted():
+    P = lattice_batch([64, 64], q.QMC_FP32, seed=60)
+    before = P.pos.clone()
+    r = P.d[1]
+    P.pos[r.offset + 5] = float("nan")
+    lp, sw, acc = zeros(P.W), zeros(P.W, torch.int64), zeros((P.W, 8))
+    q.qmc_sweep(P.d, q.options(), P.pos, lp, sw, 3, 2, 0, acc)
+    with pytest.raises(q.QmcError, match="DEVICE"):
+        q.qmc_status(timeout_ms=60000)
+    assert q.qmc_status(timeout_ms=60000) == 0  # the word is cleared by reading it
+    host = P.pos.cpu()
+    assert not torch.equal(host[:3 * 64], before[:3 * 64].cpu())       # walker 0 moved
+    assert torch.equal(host[r.offset + 6:r.offset + 3 * 64], before[r.offset + 6:r.offset + 3 * 64].cpu())
+    assert sw.cpu().tolist() == [2, 0]
