@@ -21,7 +21,8 @@
  *               (per host thread).  Argument and capacity errors are detected before anything
  *               is enqueued, so no output or position is touched.  Faults found by a kernel
  *               (a non-finite coordinate or ratio) set a device error word that qmc_status()
- *               reads; a walker that trips it stops and writes nothing back.
+ *               reads; a walker that trips it stops and writes back neither its positions nor
+ *               its ln psi and sweep counter (energy samples it took before stay in accum).
  *  Threads:     calls may come from several host threads; the descriptor cache is locked.
  *
  * Citations are to sections and equations of the paper.

@@ -269,7 +269,7 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, T *sx, T *sy,
 
     double lp = a.logpsi[slot];
     const unsigned long long k0 = a.sweep[slot];
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double *A = a.accum + 8 * (size_t)slot;
     int nacc = 0;
     int last_s = -1;
     T lx = 0, ly = 0, lz = 0;
@@ -352,24 +352,24 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, T *sx, T *sy,
         if (a.energy_every > 0 && (kk + 1) % (unsigned long long)a.energy_every == 0) {
             double e[5];
             group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, a.h2m, redD, phD, bar_id, gtid, e);
-            acc[0] += e[4];
-            acc[1] += e[4] * e[4];
-            acc[2] += e[0];
-            acc[3] += e[1];
-            acc[4] += e[2];
-            acc[5] += e[3];
-            acc[6] += 1.0;
+            // added sample by sample, so a run split over several calls sums in the same order
+            if (gtid == 0) {
+                A[0] += e[4];
+                A[1] += e[4] * e[4];
+                A[2] += e[0];
+                A[3] += e[1];
+                A[4] += e[2];
+                A[5] += e[3];
+                A[6] += 1.0;
+            }
         }
     }
     group_sync<TPW>(bar_id);
     store_walker<T, TPW>(gx, n, pad, sx, sy, sz, gtid);
     if (gtid == 0) {
-        acc[7] = (double)nacc;
+        A[7] += (double)nacc;  // integer-valued: exact in any order
         a.logpsi[slot] = lp;
         a.sweep[slot] = k0 + (unsigned long long)a.nsweeps;
-        double *A = a.accum + 8 * (size_t)slot;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) A[q] += acc[q];
     }
 }
 

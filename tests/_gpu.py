@@ -65,3 +65,14 @@ def lattice_batch(ns, precision, seed=0, rho=qi.RHO_HE, bs=None, **kw):
 
 def zeros(shape, dtype=torch.float64):
     return torch.zeros(shape, dtype=dtype, device="cuda")
+
+
+def energy_scale(e):
+    """Scale of each local-energy output for a relative comparison: its own magnitude for V,
+    T_PB and T_F; for T_L = -(hbar^2/2m)(sum lap + sum |F|^2) the magnitudes of the two sums it
+    cancels (2|T_PB| + |T_F|); for E_L = V + T_L those plus |V|."""
+    e = np.asarray(e, dtype=float)
+    s = np.abs(e).copy()
+    s[1] = 2 * abs(e[2]) + abs(e[3])
+    s[4] = abs(e[0]) + s[1]
+    return np.maximum(s, 1e-12)

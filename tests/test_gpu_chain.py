@@ -15,7 +15,7 @@ import torch
 import oracle
 import paper_1312_1282_gb300 as q
 import qmc_inputs as qi
-from tests._gpu import H2M, lattice_batch, zeros
+from tests._gpu import H2M, energy_scale, lattice_batch, zeros
 
 pytestmark = pytest.mark.gpu
 
@@ -173,7 +173,5 @@ def test_full_size_sampled_walkers():
         else:
             assert np.abs(mg).min() < 1e-3
         e = oracle.local_energy(blk1, L, qi.B_HE, 5.0, 1, H2M)
-        scale = np.abs(e).copy()
-        scale[4] = abs(e[0]) + abs(e[1])
-        assert np.all(np.abs(a[w, [2, 3, 4, 5, 0]] - e) <= 1e-5 * scale)
+        assert np.all(np.abs(a[w, [2, 3, 4, 5, 0]] - e) <= 1e-5 * energy_scale(e))
     assert matched >= 2

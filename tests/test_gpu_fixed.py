@@ -11,7 +11,7 @@ import torch
 import oracle
 import paper_1312_1282_gb300 as q
 import qmc_inputs as qi
-from tests._gpu import H2M, Packed, lattice_batch, zeros
+from tests._gpu import H2M, Packed, energy_scale, lattice_batch, zeros
 
 pytestmark = pytest.mark.gpu
 
@@ -36,10 +36,8 @@ def test_local_energy(prec, sym, m):
     got = out.cpu().numpy()
     for w in range(P.W):
         want = oracle.local_energy(P.confs[w], P.Ls[w], P.bs[w], m, sym, H2M)
-        # E_L = V + T_L is compared on the scale of the two terms it is built from
-        scale = np.abs(want).copy()
-        scale[4] = abs(want[0]) + abs(want[1])
-        _close(got[w], want, TOL[prec], np.maximum(scale, 1e-12))
+        # T_L and E_L are differences: compared on the scale of the sums they are built from
+        _close(got[w], want, TOL[prec], energy_scale(want))
 
 
 @pytest.mark.parametrize("prec", PREC)
@@ -65,7 +63,7 @@ def test_energy_grad(prec):
         # derivatives of E_L are sums of kinetic terms with both signs: their scale is the
         # kinetic magnitude times the derivative's own factor
         kin = 0.5 * H2M * (np.abs(lap).sum() + (F ** 2).sum())
-        scale = np.array([abs(want[0]), abs(e[0]) + abs(e[1]), abs(want[2]), abs(want[3]) + 1e-300,
+        scale = np.array([abs(want[0]), energy_scale(e)[4], abs(want[2]), abs(want[3]) + 1e-300,
                           kin * 5.0 / P.bs[w] * 2, kin * 4.0])
         tol = TOL[prec] * (20 if prec == q.QMC_FP32 else 1)
         _close(got[w], want, tol, np.maximum(scale, 1e-12))
@@ -130,7 +128,8 @@ def test_padding_is_ignored_and_left_alone():
 
 def test_capacity_and_argument_errors():
     big = lattice_batch([2], q.QMC_FP32)
-    rows = [(q.qmc_capacity(q.QMC_FP32) + 8, q.qmc_capacity(q.QMC_FP32) + 8, 0, 0, 100.0, 0, 3.07, 5.0, 0.8)]
+    over = q.qmc_capacity(q.QMC_FP32) + 1000
+    rows = [(over, over, 0, 0, 100.0, 0, 3.07, 5.0, 0.8)]
     with pytest.raises(q.QmcError, match="CAPACITY"):
         q.qmc_local_energy(q.descs(rows), q.options(), big.pos, zeros(5))
     rows = [(10000, 10000, 0, 0, 77.0, 0, 3.07, 5.0, 0.8)]
