@@ -163,6 +163,35 @@ int qmc_trial_delta(const qmc_walker_desc *d, int W, const qmc_options *opt, con
 int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos,
                  void *stream, int *tpw_out);
 
+/*
+ * qmc_sweep_static -- qmc_sweep for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a service of the library.  Some callers cannot call
+ * cudaMalloc at all: code running while its device memory is fully reserved by another
+ * allocator, code that must not trigger the implicit synchronisation of an allocation, or
+ * hosts that forbid runtime allocation.  qmc_sweep itself allocates a walker table and an
+ * error word on first use of a batch; this entry point instead keeps its walker table, its
+ * processing order and its error word in one fixed array in device memory that is part of
+ * the library image (QMC_STATIC_SCRATCH_BYTES, about 304 KiB, held by every GPU that loads
+ * the library until the process exits).  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   Arguments and results are those of qmc_sweep, plus
+ *   err      optional device uint32 that receives QMC_DEVERR_* bits of this call (OR-ed into
+ *            it); if NULL the bits go to a word in the fixed array, which is cleared at the
+ *            start of every call and cannot be read back.
+ *   W        at most QMC_STATIC_MAX_WALKERS; larger batches are rejected with QMC_ERR_ARG.
+ * The first call on a device looks up the fixed array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call overwrites the whole array:
+ * calls whose work overlaps on the GPU (on different streams without ordering) race on it and
+ * must not be issued.  Calls on one stream are ordered and safe.  The descriptors are copied
+ * from host memory with cudaMemcpyAsync from a staging area inside the library, so two host
+ * threads calling at once are serialised while they enqueue.
+ */
+#define QMC_STATIC_MAX_WALKERS 4096
+#define QMC_STATIC_SCRATCH_BYTES (QMC_STATIC_MAX_WALKERS * 76 + 256)
+int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_options *opt, void *pos, double *logpsi,
+                     uint64_t *sweep, uint64_t seed, int nsweeps, int energy_every, double *accum,
+                     uint32_t *err, void *stream);
+
 /* Largest n one walker may have at this precision (shared-memory capacity of one CTA). */
 int qmc_capacity(int precision);
 

@@ -22,12 +22,13 @@ from . import build as _build
 __all__ = [
     "QMC_FP32", "QMC_FP64", "QMC_CUBE", "QMC_GAUSS", "QmcError", "WalkerDesc", "Options", "lib", "descs",
     "options", "qmc_init_walkers", "qmc_sweep", "qmc_local_energy", "qmc_energy_grad", "qmc_log_psi",
-    "qmc_trial_delta", "qmc_autotune", "qmc_capacity", "qmc_status", "qmc_launch_count", "qmc_version",
+    "qmc_trial_delta", "qmc_sweep_static", "QMC_STATIC_MAX_WALKERS", "qmc_autotune", "qmc_capacity", "qmc_status", "qmc_launch_count", "qmc_version",
     "qmc_shutdown", "Batch", "QmcGrad", "ACCUM_FIELDS", "ENERGY_FIELDS", "GRAD_FIELDS",
 ]
 
 QMC_FP32, QMC_FP64 = 0, 1
 QMC_CUBE, QMC_GAUSS = 0, 1
+QMC_STATIC_MAX_WALKERS = 4096
 ACCUM_FIELDS = ("sum_EL", "sum_EL2", "sum_V", "sum_TL", "sum_TPB", "sum_TF", "samples", "accepted")
 ENERGY_FIELDS = ("V", "T_L", "T_PB", "T_F", "E_L")
 GRAD_FIELDS = ("logpsi", "E_L", "dlogpsi_db", "dlogpsi_dm", "dEL_db", "dEL_dm")
@@ -77,6 +78,7 @@ def lib():
         L.qmc_log_psi.argtypes = [D, C.c_int, O, _VP, _VP, _VP]
         L.qmc_trial_delta.argtypes = [D, C.c_int, O, _VP, _VP, _VP, C.c_int, _VP, _VP]
         L.qmc_autotune.argtypes = [D, C.c_int, O, _VP, _VP, C.POINTER(C.c_int)]
+        L.qmc_sweep_static.argtypes = [D, C.c_int, O, _VP, _VP, _VP, C.c_uint64, C.c_int, C.c_int, _VP, _VP, _VP]
         L.qmc_capacity.argtypes = [C.c_int]
         L.qmc_status.argtypes = [_VP, C.c_int, C.POINTER(C.c_uint32)]
         L.qmc_launch_count.restype = C.c_uint64
@@ -141,6 +143,13 @@ def qmc_init_walkers(d, seed, jitter_sigma, opt, pos, stream=None):
 def qmc_sweep(d, opt, pos, logpsi, sweep, seed, nsweeps, energy_every, accum, stream=None):
     return _check(lib().qmc_sweep(d, len(d), C.byref(opt), _ptr(pos), _ptr(logpsi), _ptr(sweep), seed, nsweeps,
                                   energy_every, _ptr(accum), _stream(stream)))
+
+
+def qmc_sweep_static(d, opt, pos, logpsi, sweep, seed, nsweeps, energy_every, accum, err=None, stream=None):
+    """qmc_sweep without any device allocation by the library (fixed scratch array; at most
+    QMC_STATIC_MAX_WALKERS walkers; calls overlapping on the GPU must not be issued)."""
+    return _check(lib().qmc_sweep_static(d, len(d), C.byref(opt), _ptr(pos), _ptr(logpsi), _ptr(sweep), seed,
+                                         nsweeps, energy_every, _ptr(accum), _ptr(err), _stream(stream)))
 
 
 def qmc_local_energy(d, opt, pos, out, stream=None):

@@ -580,3 +580,152 @@ void qmc_shutdown(void)
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------------------------
+// qmc_sweep_static: the same sweep with every piece of device scratch in one fixed array of
+// the library image, for callers that cannot allocate device memory (see include/qmc.h).
+// Layout of the array: DevWalker table [QMC_STATIC_MAX_WALKERS] | order [QMC_STATIC_MAX_WALKERS]
+// | error word.  Host code must not use the array's name as an address: on the host it is a
+// stand-in symbol.  Its device address is looked up once per device with cudaGetSymbolAddress.
+// ----------------------------------------------------------------------------------------------
+static_assert(sizeof(DevWalker) == 72, "DevWalker layout");
+static_assert(QMC_STATIC_SCRATCH_BYTES >= QMC_STATIC_MAX_WALKERS * (sizeof(DevWalker) + sizeof(int)) + 256,
+              "static scratch size");
+static __device__ __align__(256) unsigned char g_static_scratch[QMC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_static_mu;                                   // guards the staging area below
+unsigned char *g_static_dev[MAX_DEVICES];                 // device address of g_static_scratch
+DevWalker g_static_walkers[QMC_STATIC_MAX_WALKERS];       // host staging of the table
+int g_static_order[QMC_STATIC_MAX_WALKERS];               // host staging of the order
+
+int static_setup(int dev, unsigned char *&base)
+{
+    // caller holds g_static_mu; `dev` is the current device
+    if (!g_static_dev[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_dev[dev] = static_cast<unsigned char *>(p);
+    }
+    base = g_static_dev[dev];
+    return QMC_OK;
+}
+
+// Validate one descriptor into a table entry (the checks of resolve(), without containers).
+int static_entry(const qmc_walker_desc &x, int w, const qmc_options *o, DevWalker &v)
+{
+    if (x.n < 2) return fail(QMC_ERR_ARG, "walker %d: n = %d < 2", w, x.n);
+    if (x.pad_n < x.n || x.pad_n % 4) return fail(QMC_ERR_ARG, "walker %d: pad_n must be >= n and a multiple of 4", w);
+    if (x.offset < 0 || x.offset % 4) return fail(QMC_ERR_ARG, "walker %d: offset must be >= 0 and a multiple of 4", w);
+    double L = x.L;
+    if (!(L > 0)) {
+        if (!is_fin(x.rho) || x.rho <= 0) return fail(QMC_ERR_ARG, "walker %d: need L > 0 or rho > 0", w);
+        L = std::cbrt((double)x.n / x.rho);
+    }
+    if (!is_fin(L)) return fail(QMC_ERR_ARG, "walker %d: non-finite box side", w);
+    if (!is_fin(x.b) || x.b < 0) return fail(QMC_ERR_ARG, "walker %d: b must be finite and >= 0", w);
+    if (!is_fin(x.m_exp) || x.m_exp <= 0) return fail(QMC_ERR_ARG, "walker %d: m_exp must be finite and > 0", w);
+    if (!is_fin(x.step) || x.step <= 0) return fail(QMC_ERR_ARG, "walker %d: step must be finite and > 0", w);
+    const double reach = o->proposal == QMC_CUBE ? x.step : 6.8 * x.step;
+    if (reach >= L) return fail(QMC_ERR_ARG, "walker %d: step too large for box side %g", w, L);
+    v.n = x.n;
+    v.pad = x.pad_n;
+    v.off = x.offset;
+    v.wid = (uint32_t)x.id;
+    v.slot = w;
+    v.L = L;
+    v.b = x.b;
+    v.m = x.m_exp;
+    v.step = x.step;
+    v.c = -0.5 * std::pow(x.b, x.m_exp);
+    v.K = o->sym ? 2.0 * v.c * std::pow(2.0 / L, x.m_exp) : 0.0;
+    return QMC_OK;
+}
+
+}  // namespace
+
+extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_options *opt, void *pos, double *logpsi,
+                                uint64_t *sweep, uint64_t seed, int nsweeps, int energy_every, double *accum,
+                                uint32_t *err, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = check_options(opt);
+    if (rc) return rc;
+    if (!d) return fail(QMC_ERR_ARG, "descriptor pointer is NULL");
+    if (W <= 0) return fail(QMC_ERR_ARG, "W must be > 0");
+    if (W > QMC_STATIC_MAX_WALKERS)
+        return fail(QMC_ERR_ARG, "qmc_sweep_static takes at most %d walkers (got %d); use qmc_sweep",
+                    QMC_STATIC_MAX_WALKERS, W);
+    if ((rc = check_ptr(pos, "pos", 16)) || (rc = check_ptr(logpsi, "logpsi", 8)) ||
+        (rc = check_ptr(sweep, "sweep", 8)) || (rc = check_ptr(accum, "accum", 8)))
+        return rc;
+    if (err && (uintptr_t)err % 4) return fail(QMC_ERR_ARG, "err must be 4-byte aligned");
+    if (nsweeps < 0) return fail(QMC_ERR_ARG, "nsweeps must be >= 0");
+    if (energy_every < 0) return fail(QMC_ERR_ARG, "energy_every must be >= 0");
+    int dev;
+    if ((rc = current_device(dev))) return rc;
+    int nsm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    unsigned char *base = nullptr;
+    if ((rc = static_setup(dev, base))) return rc;
+    Plan P;  // shape summary only: no device table, no containers filled
+    P.device = dev;
+    P.W = W;
+    P.sym = opt->sym;
+    P.maxn = P.maxpad = 0;
+    P.m5 = true;
+    for (int w = 0; w < W; ++w) {
+        if ((rc = static_entry(d[w], w, opt, g_static_walkers[w]))) return rc;
+        P.maxn = std::max(P.maxn, d[w].n);
+        P.maxpad = std::max(P.maxpad, d[w].pad_n);
+        if (d[w].m_exp != 5.0) P.m5 = false;
+        g_static_order[w] = w;
+    }
+    // longest walkers first; ties by index (std::sort works in place)
+    std::sort(g_static_order, g_static_order + W, [&](int a, int b) {
+        return d[a].n != d[b].n ? d[a].n > d[b].n : a < b;
+    });
+    const int tpw = choose_tpw(P, opt, dev, nsm);
+    if ((rc = check_capacity(P, opt->precision, tpw))) return rc;
+    if (nsweeps == 0) return QMC_OK;
+
+    DevWalker *d_walkers = reinterpret_cast<DevWalker *>(base);
+    int *d_order = reinterpret_cast<int *>(base + QMC_STATIC_MAX_WALKERS * sizeof(DevWalker));
+    unsigned *d_err = reinterpret_cast<unsigned *>(base + QMC_STATIC_MAX_WALKERS * (sizeof(DevWalker) + sizeof(int)));
+    // pageable host -> device: the staging area may be reused once these calls return
+    e = cudaMemcpyAsync(d_walkers, g_static_walkers, sizeof(DevWalker) * (size_t)W, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, g_static_order, sizeof(int) * (size_t)W, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !err) e = cudaMemsetAsync(d_err, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(e, "static walker table upload");
+
+    const int G = choose_groups(P, opt->precision, tpw, nsm);
+    SweepArgs a;
+    a.walkers = d_walkers;
+    a.order = d_order;
+    a.W = W;
+    a.G = G;
+    a.stride = P.maxpad;
+    a.pos = pos;
+    a.logpsi = logpsi;
+    a.sweep = reinterpret_cast<unsigned long long *>(sweep);
+    a.accum = accum;
+    a.seed = seed;
+    a.nsweeps = nsweeps;
+    a.energy_every = energy_every;
+    a.recompute_every = opt->recompute_every;
+    a.proposal = opt->proposal;
+    a.sequential = opt->sequential;
+    a.h2m = opt->hbar2_over_m;
+    a.err = err ? reinterpret_cast<unsigned *>(err) : d_err;
+    const int grid = (W + G - 1) / G;
+    const size_t smem = (size_t)G * smem_group(opt->precision, P.maxpad, tpw);
+    e = launch_sweep(opt->precision, tpw, variant_of(P, opt), grid, G * tpw, smem, st, a);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+    g_launches.fetch_add(1);
+    return QMC_OK;
+}
