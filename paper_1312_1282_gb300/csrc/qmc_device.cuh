@@ -135,7 +135,8 @@ template <> struct Fn<double> {
 //
 // u(r2) with SYM clamps r^2 at (L/2)^2 instead of branching: the clamped value gives
 // u(L/2) = 0 analytically, and two clamped pairs give bit-identical values, so far partners
-// cancel exactly in the old/new difference of a move.  NaN padding entries clamp the same way.
+// cancel exactly in the old/new difference of a move.  Padding entries (far coordinates, whose
+// r^2 is infinite or above the clamp) and the NaN that marks the moved atom clamp the same way.
 // ----------------------------------------------------------------------------------------------
 template <typename T, int MEXP, bool SYM> struct Jas {
     T c, K, L, hL2, m;
@@ -238,8 +239,21 @@ template <typename T> __device__ __forceinline__ T mi_abs(T d, T L)
     const T a = fabs(d);
     return fmin(a, L - a);
 }
-// signed nearest-image difference
-template <typename T> __device__ __forceinline__ T mi_signed(T d, T L, T iL) { return fma(-L, Fn<T>::rint(d * iL), d); }
+// signed nearest-image difference; the rounding to an integer uses the add/subtract of
+// 1.5 * 2^(mantissa bits), which stays on the FMA pipe (valid for |d / L| < 2^22)
+template <typename T> __device__ __forceinline__ T round_magic(T x);
+template <> __device__ __forceinline__ float round_magic<float>(float x)
+{
+    return __fadd_rn(__fadd_rn(x, 12582912.0f), -12582912.0f);
+}
+template <> __device__ __forceinline__ double round_magic<double>(double x)
+{
+    return __dadd_rn(__dadd_rn(x, 6755399441055744.0), -6755399441055744.0);
+}
+template <typename T> __device__ __forceinline__ T mi_signed(T d, T L, T iL)
+{
+    return fma(-L, round_magic<T>(d * iL), d);
+}
 // a coordinate displaced by less than one box length, put back into [0, L]
 template <typename T> __device__ __forceinline__ T wrap(T x, T L)
 {
@@ -277,9 +291,21 @@ template <int TPW, typename T> __device__ __forceinline__ T group_sum(T v, T *re
     constexpr int NW = TPW / 32;
     if ((gtid & 31) == 0) red[ph * NW + (gtid >> 5)] = v;
     group_sync<TPW>(bar_id);
-    T s = red[ph * NW];
+    T s;
+    if constexpr (sizeof(T) == 4 && NW % 4 == 0) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(red + ph * NW);
+        float4 a = r4[0];
+        s = ((a.x + a.y) + a.z) + a.w;
 #pragma unroll
-    for (int w = 1; w < NW; ++w) s += red[ph * NW + w];
+        for (int w = 1; w < NW / 4; ++w) {
+            a = r4[w];
+            s = (((s + a.x) + a.y) + a.z) + a.w;
+        }
+    } else {
+        s = red[ph * NW];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) s += red[ph * NW + w];
+    }
     ph ^= 1;
     return s;
 }

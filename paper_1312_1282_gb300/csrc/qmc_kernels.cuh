@@ -2,8 +2,9 @@
 //
 // Layout in shared memory: each walker's coordinates stay resident for a whole call as three
 // blocks x[pad] | y[pad] | z[pad] of T (structure of arrays, as in HBM), read as 16-byte vectors
-// (float4 / double2).  Entries n .. pad-1 hold NaN, which the clamped pair function turns into an
-// exact zero contribution, so the partner loops need no bound checks.
+// (float4 / double2).  Entries n .. pad-1 hold a far coordinate (1e30): its squared distance
+// overflows to infinity (FP32) or exceeds (L/2)^2, which the clamped pair function turns into an
+// exact zero contribution and the energy masks, so the partner loops need no bound checks.
 //
 // Work split: a CTA holds G walkers, each served by a group of TPW threads (TPW a multiple of
 // 32).  For one move every thread of the group evaluates the old and new pair terms of its
@@ -12,6 +13,8 @@
 // the moved atom's chunk writes its new coordinates; all other threads keep a register copy of
 // the last accepted move, so a move needs exactly one group barrier (none for TPW = 32).
 #pragma once
+
+#include <type_traits>
 
 #include "qmc_device.cuh"
 
@@ -65,16 +68,27 @@ struct SweepArgs {
     unsigned *err;
 };
 
-// shared-memory bytes of one group: positions + reduction slots (T and double, 2 phases each)
+// Moves per batch of the sweep: the partner loop serves KB trial moves at once and the group
+// reduces their KB sums with one barrier (see move_batch).  Measured on GB300 at N = 1952,
+// 528 walkers, 128 threads per walker: KB = 1 is fastest (21.8 ms per 5 sweeps; KB = 2 22.3 ms,
+// KB = 4 31.7 ms, limited by registers), so it is the default; larger KB stays available.
+#ifndef QMC_KB
+#define QMC_KB 1
+#endif
+constexpr int KB = QMC_KB;
+
+// shared-memory bytes of one group: positions, then the reduction slots (2 phases of TPW/32
+// doubles, 2 phases of KB x TPW/32 T's) and the cross terms of a batch (2 phases of KB x KB T's)
 template <typename T> __host__ __device__ constexpr size_t group_smem(int stride, int tpw)
 {
-    return (size_t)3 * stride * sizeof(T) + (size_t)2 * (tpw / 32) * (sizeof(T) + sizeof(double)) * 2;
+    return (size_t)3 * stride * sizeof(T) + (size_t)2 * (tpw / 32) * sizeof(double) +
+           (size_t)2 * KB * (tpw / 32) * sizeof(T) + (size_t)2 * KB * KB * sizeof(T) + 16;
 }
 
 // ----------------------------------------------------------------------------------------------
 // Load / store one walker
 // ----------------------------------------------------------------------------------------------
-// Copy walker coordinates to shared memory (NaN past n).  Returns false (in every thread of the
+// Copy walker coordinates to shared memory (a far coordinate past n).  Returns false (in every thread of the
 // group) if a coordinate is non-finite or outside [0, L].
 template <typename T, int TPW>
 __device__ bool load_walker(const T *gx, int n, int pad, T L, T *sx, T *sy, T *sz, T *red, int &ph, int bar_id,
@@ -96,7 +110,7 @@ __device__ bool load_walker(const T *gx, int n, int pad, T L, T *sx, T *sy, T *s
                 if (j < n) {
                     bad |= !(a >= (T)0 && a <= L);  // false for NaN
                 } else {
-                    Vec<T>::set(v[k], e, qnan<T>());
+                    Vec<T>::set(v[k], e, (T)1e30);
                 }
             }
         }
@@ -128,40 +142,43 @@ __device__ void store_walker(T *gx, int n, int pad, const T *sx, const T *sy, co
 }
 
 // ----------------------------------------------------------------------------------------------
-// Eq. (JastrowUpdate): this thread's share of sum_{j != s} [u(|r' - r_j|) - u(|r_s - r_j|)]
-// ----------------------------------------------------------------------------------------------
-template <typename T, int MEXP, bool SYM, int TPW>
-__device__ __forceinline__ T partner_delta(const Jas<T, MEXP, SYM> &J, const T *sx, const T *sy, const T *sz,
-                                           int nv, int s, T xs, T ys, T zs, T xn, T yn, T zn, int gtid)
-{
-    using V = typename Vec<T>::type;
-    constexpr int VN = Vec<T>::N;
-    const int cs = s / VN;
-    const T L = J.L;
-    T acc = (T)0;
-#pragma unroll 2
-    for (int c = gtid; c < nv; c += TPW) {
-        V X = reinterpret_cast<const V *>(sx)[c];
-        V Y = reinterpret_cast<const V *>(sy)[c];
-        V Z = reinterpret_cast<const V *>(sz)[c];
-        if (c == cs) {  // the moved atom is not its own partner
-            const int e = s - cs * VN;
-            Vec<T>::set(X, e, qnan<T>());
-            Vec<T>::set(Y, e, qnan<T>());
-            Vec<T>::set(Z, e, qnan<T>());
-        }
-#pragma unroll
-        for (int e = 0; e < VN; ++e) {
-            const T xj = Vec<T>::get(X, e), yj = Vec<T>::get(Y, e), zj = Vec<T>::get(Z, e);
-            const T ax = mi_abs(xs - xj, L), ay = mi_abs(ys - yj, L), az = mi_abs(zs - zj, L);
-            const T bx = mi_abs(xn - xj, L), by = mi_abs(yn - yj, L), bz = mi_abs(zn - zj, L);
-            const T ro = fma(ax, ax, fma(ay, ay, az * az));
-            const T rn = fma(bx, bx, fma(by, by, bz * bz));
-            acc += J.u(rn) - J.u(ro);
-        }
+// Eq. (JastrowUpdate) terms u(|r' - r_j|) - u(|r_s - r_j|), FP32, exponent 5, symmetrised u:
+// two partners per packed f32x2 instruction (FFMA2/FADD2/FMUL2 issue once for two lanes of
+// work; min/max and the SFU stay scalar).
+struct Packed5 {
+    float2 L, hL2, m1, c, nK;  // (L, L), ((L/2)^2, ...), (-1, -1), (c, c), (-K, -K)
+    __device__ __forceinline__ void init(const Jas<float, 5, true> &J)
+    {
+        L = make_float2(J.L, J.L);
+        hL2 = make_float2(J.hL2, J.hL2);
+        m1 = make_float2(-1.f, -1.f);
+        c = make_float2(J.c, J.c);
+        nK = make_float2(-J.K, -J.K);
     }
-    return acc;
-}
+    // |d| folded to the nearest image: min(|d|, L - |d|), for two differences at once
+    __device__ __forceinline__ float2 fold(float2 d) const
+    {
+        const float2 a = make_float2(fabsf(d.x), fabsf(d.y));
+        const float2 b = __ffma2_rn(a, m1, L);
+        return make_float2(fminf(a.x, b.x), fminf(a.y, b.y));
+    }
+    // u(r) of two partners from their coordinate differences (clamped at r = L/2)
+    __device__ __forceinline__ float2 u(float2 dx, float2 dy, float2 dz) const
+    {
+        const float2 mx = fold(dx), my = fold(dy), mz = fold(dz);
+        float2 r2 = __fmul2_rn(mx, mx);
+        r2 = __ffma2_rn(my, my, r2);
+        r2 = __ffma2_rn(mz, mz, r2);
+        r2 = make_float2(fminf(r2.x, hL2.x), fminf(r2.y, hL2.y));
+        const float2 q = make_float2(rsqrt_a(r2.x), rsqrt_a(r2.y));
+        const float2 r = __fmul2_rn(r2, q);
+        const float2 w = __ffma2_rn(r, m1, L);
+        const float2 iw = make_float2(rcp_a(w.x), rcp_a(w.y));
+        const float2 q2 = __fmul2_rn(q, q), w2 = __fmul2_rn(iw, iw);
+        const float2 q5 = __fmul2_rn(__fmul2_rn(q2, q2), q), w5 = __fmul2_rn(__fmul2_rn(w2, w2), iw);
+        return __ffma2_rn(c, q5, __ffma2_rn(c, w5, nK));
+    }
+};
 
 // ----------------------------------------------------------------------------------------------
 // Group-wide O(N^2) passes over the resident configuration
@@ -196,7 +213,11 @@ __device__ double group_log_psi(const Jas<T, MEXP, SYM> &J, const T *sx, const T
     return 0.5 * group_sum<TPW>(tot, redD, phD, bar_id, gtid);
 }
 
-// Local energy pieces (Sec. 2 Hamiltonian): sums over i of V_i (full rows), lap_i and |F_i|^2.
+// Local energy pieces (Sec. 2 Hamiltonian).  Rows i are spread over the group one warp-block of
+// 32 consecutive rows at a time; partners j are read as broadcast 16-byte chunks.  The drift
+// F_i = sum_j u'(r) (r_i - r_j)/r needs every ordered pair; V and the Laplacian term
+// u'' + 2u'/r are symmetric, so they are taken once per pair (j > i) and the warp skips them
+// for chunks that lie wholly at or below its block's first row.
 // out = {V, T_L, T_PB, T_F, E_L}, valid in every thread of the group.
 template <typename T, int MEXP, bool SYM, int TPW>
 __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *sy, const T *sz, int n, int nv,
@@ -204,46 +225,288 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
 {
     using V = typename Vec<T>::type;
     constexpr int VN = Vec<T>::N;
-    const T L = J.L, iL = (T)1 / J.L, hL2 = J.hL2;
+    const T L = J.L, iL = (T)1 / J.L, hL2 = J.hL2, m = J.m, mm1 = J.m * (J.m + (T)1);
+    const int lane = gtid & 31;
     double sV = 0.0, sLap = 0.0, sF2 = 0.0;
-    for (int i = gtid; i < n; i += TPW) {
-        const T xi = sx[i], yi = sy[i], zi = sz[i];
+    for (int i0 = gtid - lane; i0 < n; i0 += TPW) {  // warp-uniform
+        const int i = i0 + lane;
+        const bool row = i < n;
+        const int ii = row ? i : n - 1;
+        const T xi = sx[ii], yi = sy[ii], zi = sz[ii];
         T v = 0, lap = 0, fx = 0, fy = 0, fz = 0;
         for (int c = 0; c < nv; ++c) {
             const V X = reinterpret_cast<const V *>(sx)[c];
             const V Y = reinterpret_cast<const V *>(sy)[c];
             const V Z = reinterpret_cast<const V *>(sz)[c];
+            const bool upper = c * VN + VN - 1 > i0;  // some lane of the warp has j > i here
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
+                const int j = c * VN + e;
                 const T dx = mi_signed(xi - Vec<T>::get(X, e), L, iL);
                 const T dy = mi_signed(yi - Vec<T>::get(Y, e), L, iL);
                 const T dz = mi_signed(zi - Vec<T>::get(Z, e), L, iL);
                 const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                const bool ok = (r2 < hL2) && (c * VN + e != i);
-                T q, u1, u2;
-                J.d12(r2, q, u1, u2);
-                const T vv = aziz(r2 * q, q);
-                const T g = u1 * q;
-                v += ok ? vv : (T)0;
-                lap += ok ? fma((T)2 * u1, q, u2) : (T)0;
-                fx += ok ? g * dx : (T)0;
-                fy += ok ? g * dy : (T)0;
-                fz += ok ? g * dz : (T)0;
+                const bool ok = (r2 < hL2) && (j != i);
+                const T q = Fn<T>::rsqrt(r2);
+                const T r = r2 * q;
+                const T f0 = J.fq(q, r);  // f(r) = c r^-m
+                T u1 = -m * f0 * q, u2 = mm1 * f0 * (q * q);
+                if (SYM) {
+                    const T w = L - r, iw = Fn<T>::rcp(w);
+                    const T g0 = J.fq(iw, w);  // f(L - r)
+                    u1 += m * g0 * iw;
+                    u2 += mm1 * g0 * (iw * iw);
+                }
+                const T g = ok ? u1 * q : (T)0;
+                fx = fma(g, dx, fx);
+                fy = fma(g, dy, fy);
+                fz = fma(g, dz, fz);
+                if (upper) {
+                    const bool half = ok && j > i;
+                    lap += half ? fma((T)2 * u1, q, u2) : (T)0;
+                    v += half ? aziz(r, q) : (T)0;
+                }
             }
         }
-        sV += (double)v;
-        sLap += (double)lap;
-        sF2 += (double)fx * fx + (double)fy * fy + (double)fz * fz;
+        if (row) {
+            sV += (double)v;
+            sLap += 2.0 * (double)lap;  // each pair's Laplacian term belongs to both atoms
+            sF2 += (double)fx * fx + (double)fy * fy + (double)fz * fz;
+        }
     }
     sV = group_sum<TPW>(sV, redD, phD, bar_id, gtid);
     sLap = group_sum<TPW>(sLap, redD, phD, bar_id, gtid);
     sF2 = group_sum<TPW>(sF2, redD, phD, bar_id, gtid);
     const double k = 0.5 * h2m;
-    out[0] = 0.5 * sV;
+    out[0] = sV;
     out[1] = -k * (sLap + sF2);
     out[2] = -0.5 * k * sLap;
     out[3] = k * sF2;
     out[4] = out[0] + out[1];
+}
+
+// ----------------------------------------------------------------------------------------------
+// Batched moves.  A batch of K consecutive trial moves (distinct atoms s_0..s_{K-1}) is
+// evaluated against the configuration X at the start of the batch: for every partner j the
+// partner loop adds u(|b_i - r_j|) - u(|a_i - r_j|) to S_i, where a_i = r_{s_i} and
+// b_i = wrap(a_i + delta_i).  The decisions are then taken in order; if move k < i was accepted,
+// atom s_k sits at b_k instead of a_k when move i is tried, which changes exactly one term of
+// Delta_i by
+//     D_ik = [u(|b_i - b_k|) - u(|a_i - b_k|)] - [u(|b_i - a_k|) - u(|a_i - a_k|)],
+// computed during the same loop by the thread that owns atom s_k's chunk.  So
+// Delta_i = S_i + sum_{k < i, accepted} D_ik is Eq. (JastrowUpdate) for the true configuration.
+// A batch that draws the same atom twice is done one move at a time.
+// ----------------------------------------------------------------------------------------------
+template <typename T, int KM> struct Recent {  // accepted moves of the previous batch (register copy)
+    int s[KM];
+    T x[KM], y[KM], z[KM];
+    int cnt;
+    __device__ __forceinline__ void clear() { cnt = 0; }
+    __device__ __forceinline__ void lookup(int a, T &px, T &py, T &pz) const
+    {
+#pragma unroll
+        for (int q = 0; q < KM; ++q)
+            if (q < cnt && s[q] == a) {
+                px = x[q];
+                py = y[q];
+                pz = z[q];
+            }
+    }
+};
+
+template <typename T, int MEXP, bool SYM>
+__device__ __forceinline__ T pair_du(const Jas<T, MEXP, SYM> &J, T xj, T yj, T zj, T ax, T ay, T az, T bx, T by,
+                                     T bz)
+{
+    const T L = J.L;
+    const T px = mi_abs(ax - xj, L), py = mi_abs(ay - yj, L), pz = mi_abs(az - zj, L);
+    const T qx = mi_abs(bx - xj, L), qy = mi_abs(by - yj, L), qz = mi_abs(bz - zj, L);
+    return J.u(fma(qx, qx, fma(qy, qy, qz * qz))) - J.u(fma(px, px, fma(py, py, pz * pz)));
+}
+
+// This thread's partner sums S[0..K-1] of one batch; the owners of the moved atoms' chunks
+// also write the cross terms D_ik (i > k) to dsm[i * K + k].  In the partner loop every moved
+// atom is replaced by NaN, which contributes exactly zero to every sum (the clamp), so the loop
+// has a single fast path; afterwards the owner of atom s_k adds its terms as a partner of the
+// other moves, u(|b_i - a_k|) - u(|a_i - a_k|), and the cross terms.
+template <typename T, int MEXP, bool SYM, int TPW, int K>
+__device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const T *sx, const T *sy, const T *sz,
+                                               int nv, const int (&s)[K], const T (&ax)[K], const T (&ay)[K],
+                                               const T (&az)[K], const T (&bx)[K], const T (&by)[K],
+                                               const T (&bz)[K], T (&S)[K], T *dsm, int gtid)
+{
+    using V = typename Vec<T>::type;
+    constexpr int VN = Vec<T>::N;
+    int cs[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        cs[i] = s[i] / VN;
+        S[i] = (T)0;
+    }
+    if constexpr (std::is_same<T, float>::value && MEXP == 5 && SYM) {
+        Packed5 P;
+        P.init(J);
+        float2 nax[K], nay[K], naz[K], nbx[K], nby[K], nbz[K], acc[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            nax[i] = make_float2(-ax[i], -ax[i]);
+            nay[i] = make_float2(-ay[i], -ay[i]);
+            naz[i] = make_float2(-az[i], -az[i]);
+            nbx[i] = make_float2(-bx[i], -bx[i]);
+            nby[i] = make_float2(-by[i], -by[i]);
+            nbz[i] = make_float2(-bz[i], -bz[i]);
+            acc[i] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 2
+        for (int c = gtid; c < nv; c += TPW) {
+            float4 X = reinterpret_cast<const float4 *>(sx)[c];
+            float4 Y = reinterpret_cast<const float4 *>(sy)[c];
+            float4 Z = reinterpret_cast<const float4 *>(sz)[c];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (c == cs[k]) {
+                    const int e = s[k] - 4 * c;
+                    Vec<float>::set(X, e, qnan<float>());
+                    Vec<float>::set(Y, e, qnan<float>());
+                    Vec<float>::set(Z, e, qnan<float>());
+                }
+            const float2 xa = make_float2(X.x, X.y), xb = make_float2(X.z, X.w);
+            const float2 ya = make_float2(Y.x, Y.y), yb = make_float2(Y.z, Y.w);
+            const float2 za = make_float2(Z.x, Z.y), zb = make_float2(Z.z, Z.w);
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const float2 oa = P.u(__fadd2_rn(xa, nax[i]), __fadd2_rn(ya, nay[i]), __fadd2_rn(za, naz[i]));
+                const float2 na = P.u(__fadd2_rn(xa, nbx[i]), __fadd2_rn(ya, nby[i]), __fadd2_rn(za, nbz[i]));
+                const float2 ob = P.u(__fadd2_rn(xb, nax[i]), __fadd2_rn(yb, nay[i]), __fadd2_rn(zb, naz[i]));
+                const float2 nb = P.u(__fadd2_rn(xb, nbx[i]), __fadd2_rn(yb, nby[i]), __fadd2_rn(zb, nbz[i]));
+                acc[i] = __fadd2_rn(acc[i], __ffma2_rn(oa, P.m1, na));
+                acc[i] = __fadd2_rn(acc[i], __ffma2_rn(ob, P.m1, nb));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < K; ++i) S[i] = acc[i].x + acc[i].y;
+    } else {
+#pragma unroll 2
+        for (int c = gtid; c < nv; c += TPW) {
+            V X = reinterpret_cast<const V *>(sx)[c];
+            V Y = reinterpret_cast<const V *>(sy)[c];
+            V Z = reinterpret_cast<const V *>(sz)[c];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (c == cs[k]) {
+                    const int e = s[k] - VN * c;
+                    Vec<T>::set(X, e, qnan<T>());
+                    Vec<T>::set(Y, e, qnan<T>());
+                    Vec<T>::set(Z, e, qnan<T>());
+                }
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const T xj = Vec<T>::get(X, e), yj = Vec<T>::get(Y, e), zj = Vec<T>::get(Z, e);
+#pragma unroll
+                for (int i = 0; i < K; ++i) S[i] += pair_du(J, xj, yj, zj, ax[i], ay[i], az[i], bx[i], by[i], bz[i]);
+            }
+        }
+    }
+    if constexpr (K > 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (gtid == cs[k] % TPW) {
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    if (i == k) continue;
+                    const T t = pair_du(J, ax[k], ay[k], az[k], ax[i], ay[i], az[i], bx[i], by[i], bz[i]);
+                    S[i] += t;
+                    if (i > k) dsm[i * K + k] = pair_du(J, bx[k], by[k], bz[k], ax[i], ay[i], az[i], bx[i], by[i], bz[i]) - t;
+                }
+            }
+    }
+}
+
+// Sum K values over the group with one barrier (identical in every thread).  red holds
+// 2 phases x K x (TPW/32) slots.
+template <int TPW, int K, typename T> __device__ __forceinline__ void group_sum_k(T (&v)[K], T *red, int ph, int bar_id, int gtid)
+{
+#pragma unroll
+    for (int i = 0; i < K; ++i) v[i] = warp_sum(v[i]);
+    if (TPW == 32) {
+        __syncwarp();
+        return;
+    }
+    constexpr int NW = TPW / 32;
+    T *r = red + ph * K * NW;
+    if ((gtid & 31) == 0) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) r[i * NW + (gtid >> 5)] = v[i];
+    }
+    group_sync<TPW>(bar_id);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        T t = r[i * NW];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) t += r[i * NW + w];
+        v[i] = t;
+    }
+}
+
+// One batch of K moves.  Returns false on a non-finite ratio (identically in every thread).
+template <typename T, int MEXP, bool SYM, int TPW, int K, int KM>
+__device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T *sy, T *sz, int nv,
+                                           const int (&s)[K], const T (&dx)[K], const T (&dy)[K], const T (&dz)[K],
+                                           const T (&xi)[K], Recent<T, KM> &rec, double &lp, int &nacc, T *red,
+                                           T *dsm_base, int &ph, int bar_id, int gtid)
+{
+    constexpr int VN = Vec<T>::N;
+    const T L = J.L;
+    T ax[K], ay[K], az[K], bx[K], by[K], bz[K], S[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        ax[i] = sx[s[i]];
+        ay[i] = sy[s[i]];
+        az[i] = sz[s[i]];
+        rec.lookup(s[i], ax[i], ay[i], az[i]);
+        bx[i] = wrap(ax[i] + dx[i], L);
+        by[i] = wrap(ay[i] + dy[i], L);
+        bz[i] = wrap(az[i] + dz[i], L);
+    }
+    T *dsm = dsm_base + ph * KM * KM;
+    batch_partners<T, MEXP, SYM, TPW, K>(J, sx, sy, sz, nv, s, ax, ay, az, bx, by, bz, S, dsm, gtid);
+    group_sum_k<TPW, K>(S, red, ph, bar_id, gtid);
+    ph ^= 1;
+    bool acc[K];
+    rec.clear();
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        T delta = S[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k)
+            if (acc[k]) delta += dsm[i * K + k];
+        if (delta != delta) return false;
+        // Eq. (Decision): accept iff |psi'|^2 / |psi|^2 = exp(2 Delta) > xi
+        if constexpr (std::is_same<T, float>::value)
+            acc[i] = 2.f * delta > xi[i];  // xi holds ln xi for FP32
+        else
+            acc[i] = exp(2.0 * delta) > xi[i];
+        if (acc[i]) {
+            if (gtid == 0) lp += (double)delta;
+            ++nacc;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+        if (acc[i]) {
+            if (gtid == (s[i] / VN) % TPW) {
+                sx[s[i]] = bx[i];
+                sy[s[i]] = by[i];
+                sz[s[i]] = bz[i];
+            }
+            rec.s[rec.cnt] = s[i];
+            rec.x[rec.cnt] = bx[i];
+            rec.y[rec.cnt] = by[i];
+            rec.z[rec.cnt] = bz[i];
+            ++rec.cnt;
+        }
+    if (TPW == 32) __syncwarp();
+    return true;
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -271,10 +534,12 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, T *sx, T *sy,
     const unsigned long long k0 = a.sweep[slot];
     double *A = a.accum + 8 * (size_t)slot;
     int nacc = 0;
-    int last_s = -1;
-    T lx = 0, ly = 0, lz = 0;
+    Recent<T, KB> rec;
+    rec.clear();
     const int lane = gtid & 31;
     const uint32_t wid = d.wid;
+    constexpr int NW = TPW / 32;
+    T *dsm = redT + 2 * KB * NW;  // cross terms of a batch, after the reduction slots
 
     for (int it = 0; it < a.nsweeps; ++it) {
         const unsigned long long kk = k0 + (unsigned long long)it;
@@ -306,47 +571,56 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, T *sx, T *sy,
                 const uint4 rd = philox(((uint32_t)t0 >> 2) + (uint32_t)(lane >> 2), k, wid, ST_DICE, a.seed);
                 mxi = Rng<T>::unif(word(rd, lane & 3));
             }
+            // FP32: the decision is taken as 2 Delta > ln xi, with ln xi computed here once per move
+            if constexpr (std::is_same<T, float>::value) mxi = logf(mxi);
             const int cnt = min(32, n - t0);
-            for (int tt = 0; tt < cnt; ++tt) {
-                const int s = __shfl_sync(FULL, my_s, tt);
-                const T dx = __shfl_sync(FULL, mdx, tt);
-                const T dy = __shfl_sync(FULL, mdy, tt);
-                const T dz = __shfl_sync(FULL, mdz, tt);
-                const T xi = __shfl_sync(FULL, mxi, tt);
-                T xs = sx[s], ys = sy[s], zs = sz[s];
-                if (s == last_s) {
-                    xs = lx;
-                    ys = ly;
-                    zs = lz;
+            int tt = 0;
+            for (; tt + KB <= cnt; tt += KB) {
+                int bs[KB];
+                T bdx[KB], bdy[KB], bdz[KB], bxi[KB];
+#pragma unroll
+                for (int i = 0; i < KB; ++i) {
+                    bs[i] = __shfl_sync(FULL, my_s, tt + i);
+                    bdx[i] = __shfl_sync(FULL, mdx, tt + i);
+                    bdy[i] = __shfl_sync(FULL, mdy, tt + i);
+                    bdz[i] = __shfl_sync(FULL, mdz, tt + i);
+                    bxi[i] = __shfl_sync(FULL, mxi, tt + i);
                 }
-                const T xn = wrap(xs + dx, L), yn = wrap(ys + dy, L), zn = wrap(zs + dz, L);
-                const T part = partner_delta<T, MEXP, SYM, TPW>(J, sx, sy, sz, nv, s, xs, ys, zs, xn, yn, zn, gtid);
-                const T delta = group_sum<TPW>(part, redT, phT, bar_id, gtid);
-                if (delta != delta) {  // identical in every thread of the group
+                bool distinct = true;
+#pragma unroll
+                for (int i = 0; i < KB; ++i)
+#pragma unroll
+                    for (int q = i + 1; q < KB; ++q) distinct &= bs[i] != bs[q];
+                bool ok = true;
+                if (distinct) {
+                    ok = move_batch<T, MEXP, SYM, TPW, KB, KB>(J, sx, sy, sz, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
+                                                               nacc, redT, dsm, phT, bar_id, gtid);
+                } else {
+                    for (int i = 0; i < KB && ok; ++i) {
+                        const int s1[1] = {bs[i]};
+                        const T x1[1] = {bdx[i]}, y1[1] = {bdy[i]}, z1[1] = {bdz[i]}, c1[1] = {bxi[i]};
+                        ok = move_batch<T, MEXP, SYM, TPW, 1, KB>(J, sx, sy, sz, nv, s1, x1, y1, z1, c1, rec, lp,
+                                                                  nacc, redT, dsm, phT, bar_id, gtid);
+                    }
+                }
+                if (!ok) {
                     if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
                     return;
                 }
-                // Eq. (Decision): accept iff |psi'|^2 / |psi|^2 = exp(2 Delta) > xi
-                if (exp((T)2 * delta) > xi) {
-                    if (gtid == (s / VN) % TPW) {
-                        sx[s] = xn;
-                        sy[s] = yn;
-                        sz[s] = zn;
-                    }
-                    last_s = s;
-                    lx = xn;
-                    ly = yn;
-                    lz = zn;
-                    lp += (double)delta;
-                    ++nacc;
-                } else {
-                    last_s = -1;
+            }
+            for (; tt < cnt; ++tt) {
+                const int s1[1] = {__shfl_sync(FULL, my_s, tt)};
+                const T x1[1] = {__shfl_sync(FULL, mdx, tt)}, y1[1] = {__shfl_sync(FULL, mdy, tt)},
+                        z1[1] = {__shfl_sync(FULL, mdz, tt)}, c1[1] = {__shfl_sync(FULL, mxi, tt)};
+                if (!move_batch<T, MEXP, SYM, TPW, 1, KB>(J, sx, sy, sz, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
+                                                          dsm, phT, bar_id, gtid)) {
+                    if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
+                    return;
                 }
-                if (TPW == 32) __syncwarp();
             }
         }
         group_sync<TPW>(bar_id);
-        last_s = -1;
+        rec.clear();
         if (a.recompute_every > 0 && (kk + 1) % (unsigned long long)a.recompute_every == 0)
             lp = group_log_psi<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, redD, phD, bar_id, gtid);
         if (a.energy_every > 0 && (kk + 1) % (unsigned long long)a.energy_every == 0) {
@@ -375,10 +649,12 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, T *sx, T *sy,
 
 // CTAs hold up to 256 threads (TPW <= 256) or exactly one group; at least 1024 resident threads
 // per SM, i.e. at most 64 registers per thread.
+// TPW = 128 (one 4-warp group per walker, a few walkers per SM) gets up to 128 registers.
 template <int TPW> constexpr int cta_bound() { return TPW > 256 ? TPW : 256; }
+template <int TPW> constexpr int min_blocks() { return TPW == 128 ? 2 : 1024 / cta_bound<TPW>(); }
 
 template <typename T, int MEXP, bool SYM, int TPW>
-__global__ void __launch_bounds__(cta_bound<TPW>(), 1024 / cta_bound<TPW>()) sweep_kernel(SweepArgs a)
+__global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_kernel(SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int g = threadIdx.x / TPW, gtid = threadIdx.x % TPW;
@@ -486,11 +762,13 @@ __global__ void __launch_bounds__(TPW) trial_kernel(PassArgs a)
             }
             continue;
         }
-        const T xs = sx[s], ys = sy[s], zs = sz[s];
-        const T xn = wrap(xs + (T)a.delta[3 * mi], L), yn = wrap(ys + (T)a.delta[3 * mi + 1], L),
-                zn = wrap(zs + (T)a.delta[3 * mi + 2], L);
-        const T part = partner_delta<T, MEXP, SYM, TPW>(J, sx, sy, sz, nv, s, xs, ys, zs, xn, yn, zn, gtid);
-        const T delta = group_sum<TPW>(part, redT, phT, 1, gtid);
+        const int s1[1] = {s};
+        const T ax[1] = {sx[s]}, ay[1] = {sy[s]}, az[1] = {sz[s]};
+        const T bx[1] = {wrap(ax[0] + (T)a.delta[3 * mi], L)}, by[1] = {wrap(ay[0] + (T)a.delta[3 * mi + 1], L)},
+                bz[1] = {wrap(az[0] + (T)a.delta[3 * mi + 2], L)};
+        T S[1];
+        batch_partners<T, MEXP, SYM, TPW, 1>(J, sx, sy, sz, nv, s1, ax, ay, az, bx, by, bz, S, nullptr, gtid);
+        const T delta = group_sum<TPW>(S[0], redT, phT, 1, gtid);
         if (gtid == 0) a.out[mi] = (double)delta;
     }
 }
