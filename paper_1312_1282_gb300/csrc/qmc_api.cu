@@ -127,9 +127,18 @@ int check_options(const qmc_options *o)
 
 size_t elem_size(int precision) { return precision == QMC_FP64 ? sizeof(double) : sizeof(float); }
 
-size_t smem_group(int precision, int stride, int tpw)
+// shared memory of one walker group: positions (the block stride is the largest pad rounded up
+// to 32), reduction scratch, and with the tiled energy pass the drift arrays
+size_t smem_group(int precision, int maxpad, int tpw, bool tile = false)
 {
-    return precision == QMC_FP64 ? group_smem<double>(stride, tpw) : group_smem<float>(stride, tpw);
+    const int stride = stride_of(maxpad);
+    return precision == QMC_FP64 ? group_smem<double>(stride, tpw, false) : group_smem<float>(stride, tpw, tile);
+}
+
+// the tiled local-energy pass (FP32) is used whenever its drift arrays fit next to G walkers
+bool use_tile(int precision, int maxpad, int tpw, int G)
+{
+    return precision == QMC_FP32 && (size_t)G * smem_group(precision, maxpad, tpw, true) <= MAX_SMEM;
 }
 
 int sites_of(int n)
@@ -287,7 +296,8 @@ int choose_groups(const Plan &P, int precision, int tpw, int nsm)
 {
     int G = 1;
     if (tpw <= 128 && P.W > 24 * nsm) G = std::min(256 / tpw, (P.W + 24 * nsm - 1) / (24 * nsm));
-    while (G > 1 && (size_t)G * smem_group(precision, P.maxpad, tpw) > MAX_SMEM) --G;
+    const bool tile = use_tile(precision, P.maxpad, tpw, 1);
+    while (G > 1 && (size_t)G * smem_group(precision, P.maxpad, tpw, tile) > MAX_SMEM) --G;
     return std::max(1, std::min(G, 8));
 }
 
@@ -355,7 +365,8 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     a.order = P.d_order;
     a.W = W;
     a.G = G;
-    a.stride = P.maxpad;
+    a.stride = stride_of(P.maxpad);
+    a.tile = use_tile(o->precision, P.maxpad, tpw, G) ? 1 : 0;
     a.pos = pos;
     a.logpsi = logpsi;
     a.sweep = reinterpret_cast<unsigned long long *>(sweep);
@@ -369,7 +380,7 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     a.h2m = o->hbar2_over_m;
     a.err = p.ds->err;
     const int grid = (W + G - 1) / G;
-    const size_t smem = (size_t)G * smem_group(o->precision, P.maxpad, tpw);
+    const size_t smem = (size_t)G * smem_group(o->precision, P.maxpad, tpw, a.tile != 0);
     cudaError_t e = launch_sweep(o->precision, tpw, variant_of(P, o), grid, G * tpw, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
     g_launches.fetch_add(1);
@@ -389,7 +400,8 @@ int pass_impl(const qmc_walker_desc *d, int W, const qmc_options *o, const void 
     PassArgs a;
     a.walkers = P.d_walkers;
     a.W = W;
-    a.stride = P.maxpad;
+    a.stride = stride_of(P.maxpad);
+    a.tile = (kind == 0 && use_tile(o->precision, P.maxpad, tpw, 1)) ? 1 : 0;
     a.pos = pos;
     a.out = out;
     a.h2m = o->hbar2_over_m;
@@ -397,7 +409,7 @@ int pass_impl(const qmc_walker_desc *d, int W, const qmc_options *o, const void 
     a.delta = delta;
     a.M = M;
     a.err = p.ds->err;
-    const size_t smem = smem_group(o->precision, P.maxpad, tpw);
+    const size_t smem = smem_group(o->precision, P.maxpad, tpw, a.tile != 0);
     cudaError_t e = launch_pass(o->precision, variant_of(P, o), kind, W, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "pass launch");
     g_launches.fetch_add(1);
@@ -527,7 +539,7 @@ int qmc_capacity(int precision)
     if (precision != QMC_FP32 && precision != QMC_FP64) return fail(QMC_ERR_ARG, "bad precision");
     const size_t es = elem_size(precision);
     const size_t red = smem_group(precision, 0, 1024);
-    return (int)(((MAX_SMEM - red) / (3 * es)) / 4 * 4);
+    return (int)(((MAX_SMEM - red) / (3 * es)) / 32 * 32);
 }
 
 int qmc_status(void *stream, int timeout_ms, uint32_t *bits)
@@ -709,7 +721,8 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     a.order = d_order;
     a.W = W;
     a.G = G;
-    a.stride = P.maxpad;
+    a.stride = stride_of(P.maxpad);
+    a.tile = use_tile(opt->precision, P.maxpad, tpw, G) ? 1 : 0;
     a.pos = pos;
     a.logpsi = logpsi;
     a.sweep = reinterpret_cast<unsigned long long *>(sweep);
@@ -723,7 +736,7 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     a.h2m = opt->hbar2_over_m;
     a.err = err ? reinterpret_cast<unsigned *>(err) : d_err;
     const int grid = (W + G - 1) / G;
-    const size_t smem = (size_t)G * smem_group(opt->precision, P.maxpad, tpw);
+    const size_t smem = (size_t)G * smem_group(opt->precision, P.maxpad, tpw, a.tile != 0);
     e = launch_sweep(opt->precision, tpw, variant_of(P, opt), grid, G * tpw, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
     g_launches.fetch_add(1);

@@ -2,9 +2,9 @@
 //
 // Layout in shared memory: each walker's coordinates stay resident for a whole call as three
 // blocks x[pad] | y[pad] | z[pad] of T (structure of arrays, as in HBM), read as 16-byte vectors
-// (float4 / double2).  Entries n .. pad-1 hold a far coordinate (1e30): its squared distance
-// overflows to infinity (FP32) or exceeds (L/2)^2, which the clamped pair function turns into an
-// exact zero contribution and the energy masks, so the partner loops need no bound checks.
+// (float4 / double2).  Entries n .. stride-1 hold distinct far coordinates: their squared
+// distances overflow to infinity (FP32) or exceed (L/2)^2, which the clamped pair function turns
+// into an exact zero contribution and the energy passes mask, so the loops need no bound checks.
 //
 // Work split: a CTA holds G walkers, each served by a group of TPW threads (TPW a multiple of
 // 32).  For one move every thread of the group evaluates the old and new pair terms of its
@@ -56,7 +56,8 @@ struct SweepArgs {
     const int *order;          // [W] processing order (longest walkers first)
     int W;
     int G;                     // walkers per CTA
-    int stride;                // shared-memory block stride (elements) = largest pad in the batch
+    int stride;                // shared-memory block stride (elements): largest pad, rounded up to 32
+    int tile;                  // 1: local energy by the tiled pass (needs the drift arrays in smem)
     void *pos;
     double *logpsi;
     unsigned long long *sweep;
@@ -77,40 +78,76 @@ struct SweepArgs {
 #endif
 constexpr int KB = QMC_KB;
 
-// shared-memory bytes of one group: positions, then the reduction slots (2 phases of TPW/32
-// doubles, 2 phases of KB x TPW/32 T's) and the cross terms of a batch (2 phases of KB x KB T's)
-template <typename T> __host__ __device__ constexpr size_t group_smem(int stride, int tpw)
+// Shared memory of one group, in this order: positions x | y | z (stride elements of T each),
+// reduction slots (2 phases of TPW/32 doubles, 2 phases of KB x TPW/32 T's), the cross terms of
+// a batch (2 phases of KB x KB T's), and with the tiled energy pass the drift components
+// Fx | Fy | Fz (stride floats each).
+struct GroupLayout {
+    size_t red, redT, dsm, F, bytes;
+};
+template <typename T> __host__ __device__ constexpr GroupLayout group_layout(int stride, int tpw, bool tile)
 {
-    return (size_t)3 * stride * sizeof(T) + (size_t)2 * (tpw / 32) * sizeof(double) +
-           (size_t)2 * KB * (tpw / 32) * sizeof(T) + (size_t)2 * KB * KB * sizeof(T) + 16;
+    GroupLayout g{};
+    g.red = (size_t)3 * stride * sizeof(T);
+    g.redT = g.red + (size_t)2 * (tpw / 32) * sizeof(double);
+    g.dsm = g.redT + (size_t)2 * KB * (tpw / 32) * sizeof(T);
+    g.F = (g.dsm + (size_t)2 * KB * KB * sizeof(T) + 15) / 16 * 16;
+    g.bytes = g.F + (tile ? (size_t)3 * stride * sizeof(float) : 0);
+    return g;
 }
+template <typename T> __host__ __device__ constexpr size_t group_smem(int stride, int tpw, bool tile = false)
+{
+    return group_layout<T>(stride, tpw, tile).bytes;
+}
+__host__ __device__ constexpr int stride_of(int maxpad) { return (maxpad + 31) / 32 * 32; }
+
+template <typename T> struct GroupMem {
+    T *sx, *sy, *sz, *redT, *dsm;
+    double *redD;
+    float *fx, *fy, *fz;
+    __device__ __forceinline__ void bind(unsigned char *base, int stride, int tpw, bool tile)
+    {
+        const GroupLayout g = group_layout<T>(stride, tpw, tile);
+        sx = reinterpret_cast<T *>(base);
+        sy = sx + stride;
+        sz = sy + stride;
+        redD = reinterpret_cast<double *>(base + g.red);
+        redT = reinterpret_cast<T *>(base + g.redT);
+        dsm = reinterpret_cast<T *>(base + g.dsm);
+        fx = reinterpret_cast<float *>(base + g.F);
+        fy = fx + stride;
+        fz = fy + stride;
+    }
+};
 
 // ----------------------------------------------------------------------------------------------
 // Load / store one walker
 // ----------------------------------------------------------------------------------------------
-// Copy walker coordinates to shared memory (a far coordinate past n).  Returns false (in every thread of the
+// Copy walker coordinates to shared memory.  Entries n .. stride-1 get distinct far coordinates
+// 1e30 (1 + j - n): any squared distance to them is infinite (FP32) or far above (L/2)^2, so the
+// pair loops treat them as absent without index checks.  Returns false (in every thread of the
 // group) if a coordinate is non-finite or outside [0, L].
 template <typename T, int TPW>
-__device__ bool load_walker(const T *gx, int n, int pad, T L, T *sx, T *sy, T *sz, T *red, int &ph, int bar_id,
-                            int gtid)
+__device__ bool load_walker(const T *gx, int n, int pad, int stride, T L, T *sx, T *sy, T *sz, T *red, int &ph,
+                            int bar_id, int gtid)
 {
     using V = typename Vec<T>::type;
     constexpr int VN = Vec<T>::N;
-    const int nv = pad / VN;
+    const int nvp = pad / VN, nvs = stride / VN;
     int bad = 0;
-    for (int c = gtid; c < nv; c += TPW) {
+    for (int c = gtid; c < nvs; c += TPW) {
         V v[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            v[k] = reinterpret_cast<const V *>(gx + (size_t)k * pad)[c];
+            if (c < nvp) v[k] = reinterpret_cast<const V *>(gx + (size_t)k * pad)[c];
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
                 const int j = c * VN + e;
-                const T a = Vec<T>::get(v[k], e);
                 if (j < n) {
+                    const T a = Vec<T>::get(v[k], e);
                     bad |= !(a >= (T)0 && a <= L);  // false for NaN
                 } else {
-                    Vec<T>::set(v[k], e, (T)1e30);
+                    Vec<T>::set(v[k], e, (T)1e30 * (T)(1 + j - n));
                 }
             }
         }
@@ -211,6 +248,164 @@ __device__ double group_log_psi(const Jas<T, MEXP, SYM> &J, const T *sx, const T
         tot += (double)row;
     }
     return 0.5 * group_sum<TPW>(tot, redD, phD, bar_id, gtid);
+}
+
+// Local energy, tiled (FP32).  Each unordered pair is evaluated once.  Atoms form blocks of 32;
+// a warp takes a tile of two blocks (a, b): lane l holds atom 32a + l, and at step t meets atom
+// 32b + ((l + t) mod 32), so the 32 lanes see 32 distinct partners.  The drift of the row atom
+// accumulates in a register; the opposite drift of the partner accumulates in a register that
+// is passed to the neighbouring lane after every step, so that after 32 steps lane l holds the
+// total for atom 32b + l.  Tiles are scheduled in the rounds of a round-robin tournament between
+// blocks: in one round every block is in at most one tile, so the warps add their tile totals
+// to the shared drift arrays without conflicts, in an order fixed by the schedule (the result
+// is bit-reproducible).  Diagonal tiles (pairs inside one block) form a last round.
+template <int MEXP, bool SYM> struct TilePair {
+    const Jas<float, MEXP, SYM> &J;
+    float L, iL, hL2, m, mm1;
+    __device__ __forceinline__ TilePair(const Jas<float, MEXP, SYM> &j)
+        : J(j), L(j.L), iL(1.f / j.L), hL2(j.hL2), m(j.m), mm1(j.m * (j.m + 1.f))
+    {
+    }
+    // drift contribution g (r_i - r_j) of the pair, its Laplacian term u'' + 2u'/r and V(r)
+    __device__ __forceinline__ void operator()(float xi, float yi, float zi, float xj, float yj, float zj, bool take,
+                                               float &gx, float &gy, float &gz, float &lap, float &v) const
+    {
+        const float dx = mi_signed(xi - xj, L, iL), dy = mi_signed(yi - yj, L, iL), dz = mi_signed(zi - zj, L, iL);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool ok = take && r2 < hL2;
+        const float q = rsqrt_a(r2);
+        const float r = r2 * q;
+        const float f0 = J.fq(q, r);
+        float u1 = -m * f0 * q, u2 = mm1 * f0 * (q * q);
+        if (SYM) {
+            const float w = L - r, iw = rcp_a(w);
+            const float g0 = J.fq(iw, w);
+            u1 += m * g0 * iw;
+            u2 += mm1 * g0 * (iw * iw);
+        }
+        const float g = ok ? u1 * q : 0.f;
+        gx = g * dx;
+        gy = g * dy;
+        gz = g * dz;
+        lap = ok ? fmaf(2.f * u1, q, u2) : 0.f;
+        // Aziz II; the damping exp(-(D/x - 1)^2) only matters for x < D: skipped when no lane needs it
+        const float eps = 10.948f, rm = 2.963f, A = 1.8443101e5f, alpha = 10.43329537f, beta = -2.27965105f,
+                    C6 = 1.36745214f, C8 = 0.42123807f, C10 = 0.17473318f, D = 1.4826f;
+        const float x = r * (1.f / rm);
+        const float y = (q * q) * (rm * rm);
+        const float disp = (y * y * y) * fmaf(fmaf(C10, y, C8), y, C6);
+        const float rep = A * Fn<float>::exp(x * fmaf(beta, x, -alpha));
+        float F = 1.f;
+        const bool damp = ok && x < D;
+        if (__any_sync(FULL, damp)) {
+            const float t = fmaf(D * rm, q, -1.f);
+            F = damp ? Fn<float>::exp(-(t * t)) : 1.f;
+        }
+        v = ok ? eps * fmaf(-F, disp, rep) : 0.f;
+    }
+};
+
+template <int MEXP, bool SYM, int TPW>
+__device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *sx, const float *sy, const float *sz,
+                                   float *Fx, float *Fy, float *Fz, int n, double h2m, double *redD, int &phD,
+                                   int bar_id, int gtid, double out[5])
+{
+    constexpr int NW = TPW / 32;
+    const int lane = gtid & 31, warp = gtid >> 5;
+    const int NB = (n + 31) >> 5;
+    const TilePair<MEXP, SYM> P(J);
+    for (int i = gtid; i < NB * 32; i += TPW) {
+        Fx[i] = 0.f;
+        Fy[i] = 0.f;
+        Fz[i] = 0.f;
+    }
+    group_sync<TPW>(bar_id);
+    double sV = 0.0, sLap = 0.0;
+    const int NBp = NB + (NB & 1);  // an even number of teams: a dummy block when NB is odd
+    for (int r = 0; r < NBp - 1; ++r) {
+        for (int k = warp; k < NBp / 2; k += NW) {
+            const int a = k == 0 ? r : (r + k) % (NBp - 1);
+            const int b = k == 0 ? NBp - 1 : (r - k + NBp - 1) % (NBp - 1);
+            if (a >= NB || b >= NB) continue;  // the dummy block
+            const int i = 32 * a + lane;
+            const float xi = sx[i], yi = sy[i], zi = sz[i];
+            float rx = 0.f, ry = 0.f, rz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, lap = 0.f, v = 0.f;
+#pragma unroll 2
+            for (int t = 0; t < 32; ++t) {
+                const int j = 32 * b + ((lane + t) & 31);
+                float gx, gy, gz, l1, v1;
+                P(xi, yi, zi, sx[j], sy[j], sz[j], true, gx, gy, gz, l1, v1);
+                rx += gx;
+                ry += gy;
+                rz += gz;
+                cx -= gx;
+                cy -= gy;
+                cz -= gz;
+                lap += l1;
+                v += v1;
+                const int src = (lane + 1) & 31;
+                cx = __shfl_sync(FULL, cx, src);
+                cy = __shfl_sync(FULL, cy, src);
+                cz = __shfl_sync(FULL, cz, src);
+            }
+            Fx[i] += rx;
+            Fy[i] += ry;
+            Fz[i] += rz;
+            const int jb = 32 * b + lane;
+            Fx[jb] += cx;
+            Fy[jb] += cy;
+            Fz[jb] += cz;
+            sV += (double)v;
+            sLap += 2.0 * (double)lap;
+        }
+        group_sync<TPW>(bar_id);
+    }
+    for (int b = warp; b < NB; b += NW) {  // pairs inside one block: steps 1..15, and 16 for half the lanes
+        const int i = 32 * b + lane;
+        const float xi = sx[i], yi = sy[i], zi = sz[i];
+        float rx = 0.f, ry = 0.f, rz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, lap = 0.f, v = 0.f;
+        for (int t = 1; t <= 16; ++t) {
+            const int j = 32 * b + ((lane + t) & 31);
+            float gx, gy, gz, l1, v1;
+            P(xi, yi, zi, sx[j], sy[j], sz[j], t < 16 || lane < 16, gx, gy, gz, l1, v1);
+            rx += gx;
+            ry += gy;
+            rz += gz;
+            cx -= gx;
+            cy -= gy;
+            cz -= gz;
+            lap += l1;
+            v += v1;
+            if (t < 16) {
+                const int src = (lane + 1) & 31;
+                cx = __shfl_sync(FULL, cx, src);
+                cy = __shfl_sync(FULL, cy, src);
+                cz = __shfl_sync(FULL, cz, src);
+            }
+        }
+        // after step 16 lane l holds the partner total of atom 32b + ((l + 16) mod 32)
+        const int src = (lane + 16) & 31;
+        cx = __shfl_sync(FULL, cx, src);
+        cy = __shfl_sync(FULL, cy, src);
+        cz = __shfl_sync(FULL, cz, src);
+        Fx[i] += rx + cx;
+        Fy[i] += ry + cy;
+        Fz[i] += rz + cz;
+        sV += (double)v;
+        sLap += 2.0 * (double)lap;
+    }
+    group_sync<TPW>(bar_id);
+    double sF2 = 0.0;
+    for (int i = gtid; i < n; i += TPW) sF2 += (double)Fx[i] * Fx[i] + (double)Fy[i] * Fy[i] + (double)Fz[i] * Fz[i];
+    sV = group_sum<TPW>(sV, redD, phD, bar_id, gtid);
+    sLap = group_sum<TPW>(sLap, redD, phD, bar_id, gtid);
+    sF2 = group_sum<TPW>(sF2, redD, phD, bar_id, gtid);
+    const double k = 0.5 * h2m;
+    out[0] = sV;
+    out[1] = -k * (sLap + sF2);
+    out[2] = -0.5 * k * sLap;
+    out[3] = k * sF2;
+    out[4] = out[0] + out[1];
 }
 
 // Local energy pieces (Sec. 2 Hamiltonian).  Rows i are spread over the group one warp-block of
@@ -513,9 +708,10 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
 // The sweep: one group runs one walker's chain for a whole call.
 // ----------------------------------------------------------------------------------------------
 template <typename T, int MEXP, bool SYM, int TPW>
-__device__ void run_walker(const SweepArgs &a, const DevWalker &d, T *sx, T *sy, T *sz, T *redT, double *redD,
-                           int gtid, int bar_id)
+__device__ void run_walker(const SweepArgs &a, const DevWalker &d, const GroupMem<T> &mem, int gtid, int bar_id)
 {
+    T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
+    double *redD = mem.redD;
     constexpr int VN = Vec<T>::N;
     const int n = d.n, pad = d.pad, nv = (n + VN - 1) / VN;
     const int slot = d.slot;
@@ -523,7 +719,7 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, T *sx, T *sy,
     int phT = 0, phD = 0;
     T *gx = reinterpret_cast<T *>(a.pos) + d.off;
 
-    if (!load_walker<T, TPW>(gx, n, pad, L, sx, sy, sz, redT, phT, bar_id, gtid)) {
+    if (!load_walker<T, TPW>(gx, n, pad, a.stride, L, sx, sy, sz, redT, phT, bar_id, gtid)) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
         return;
     }
@@ -538,8 +734,7 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, T *sx, T *sy,
     rec.clear();
     const int lane = gtid & 31;
     const uint32_t wid = d.wid;
-    constexpr int NW = TPW / 32;
-    T *dsm = redT + 2 * KB * NW;  // cross terms of a batch, after the reduction slots
+    T *dsm = mem.dsm;  // cross terms of a batch
 
     for (int it = 0; it < a.nsweeps; ++it) {
         const unsigned long long kk = k0 + (unsigned long long)it;
@@ -625,7 +820,15 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, T *sx, T *sy,
             lp = group_log_psi<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, redD, phD, bar_id, gtid);
         if (a.energy_every > 0 && (kk + 1) % (unsigned long long)a.energy_every == 0) {
             double e[5];
-            group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, a.h2m, redD, phD, bar_id, gtid, e);
+            if constexpr (std::is_same<T, float>::value) {
+                if (a.tile)
+                    group_energy_tiled<MEXP, SYM, TPW>(J, sx, sy, sz, mem.fx, mem.fy, mem.fz, n, a.h2m, redD, phD,
+                                                       bar_id, gtid, e);
+                else
+                    group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, a.h2m, redD, phD, bar_id, gtid, e);
+            } else {
+                group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, a.h2m, redD, phD, bar_id, gtid, e);
+            }
             // added sample by sample, so a run split over several calls sums in the same order
             if (gtid == 0) {
                 A[0] += e[4];
@@ -660,15 +863,10 @@ __global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_ker
     const int g = threadIdx.x / TPW, gtid = threadIdx.x % TPW;
     const int item = blockIdx.x * a.G + g;
     if (item >= a.W) return;  // only group barriers follow, so whole groups may leave
-    constexpr int NW = TPW / 32;
-    unsigned char *base = smem + (size_t)g * group_smem<T>(a.stride, TPW);
-    T *sx = reinterpret_cast<T *>(base);
-    T *sy = sx + a.stride;
-    T *sz = sy + a.stride;
-    double *redD = reinterpret_cast<double *>(sz + a.stride);
-    T *redT = reinterpret_cast<T *>(redD + 2 * NW);
+    GroupMem<T> mem;
+    mem.bind(smem + (size_t)g * group_smem<T>(a.stride, TPW, a.tile), a.stride, TPW, a.tile);
     const DevWalker d = a.walkers[a.order[item]];
-    run_walker<T, MEXP, SYM, TPW>(a, d, sx, sy, sz, redT, redD, gtid, 1 + g);
+    run_walker<T, MEXP, SYM, TPW>(a, d, mem, gtid, 1 + g);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -678,6 +876,7 @@ struct PassArgs {
     const DevWalker *walkers;
     int W;
     int stride;
+    int tile;
     const void *pos;
     double *out;
     double h2m;
@@ -688,32 +887,21 @@ struct PassArgs {
     unsigned *err;
 };
 
-template <typename T, int TPW>
-__device__ __forceinline__ void pass_smem(unsigned char *smem, int stride, T *&sx, T *&sy, T *&sz, T *&redT,
-                                          double *&redD)
-{
-    constexpr int NW = TPW / 32;
-    sx = reinterpret_cast<T *>(smem);
-    sy = sx + stride;
-    sz = sy + stride;
-    redD = reinterpret_cast<double *>(sz + stride);
-    redT = reinterpret_cast<T *>(redD + 2 * NW);
-}
-
 // kind: 0 = local energy (5 outputs), 1 = ln psi (1 output)
 template <typename T, int MEXP, bool SYM, int TPW>
 __global__ void __launch_bounds__(TPW) pass_kernel(PassArgs a, int kind)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    T *sx, *sy, *sz, *redT;
-    double *redD;
-    pass_smem<T, TPW>(smem, a.stride, sx, sy, sz, redT, redD);
+    GroupMem<T> mem;
+    mem.bind(smem, a.stride, TPW, a.tile && kind == 0);
+    T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
+    double *redD = mem.redD;
     const DevWalker d = a.walkers[blockIdx.x];
     const int gtid = threadIdx.x;
     int phT = 0, phD = 0;
     constexpr int VN = Vec<T>::N;
     const T *gx = reinterpret_cast<const T *>(a.pos) + d.off;
-    if (!load_walker<T, TPW>(gx, d.n, d.pad, (T)d.L, sx, sy, sz, redT, phT, 1, gtid)) {
+    if (!load_walker<T, TPW>(gx, d.n, d.pad, a.stride, (T)d.L, sx, sy, sz, redT, phT, 1, gtid)) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
         return;
     }
@@ -722,7 +910,15 @@ __global__ void __launch_bounds__(TPW) pass_kernel(PassArgs a, int kind)
     const int nv = (d.n + VN - 1) / VN;
     if (kind == 0) {
         double e[5];
-        group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, d.n, nv, a.h2m, redD, phD, 1, gtid, e);
+        if constexpr (std::is_same<T, float>::value) {
+            if (a.tile)
+                group_energy_tiled<MEXP, SYM, TPW>(J, sx, sy, sz, mem.fx, mem.fy, mem.fz, d.n, a.h2m, redD, phD, 1,
+                                                   gtid, e);
+            else
+                group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, d.n, nv, a.h2m, redD, phD, 1, gtid, e);
+        } else {
+            group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, d.n, nv, a.h2m, redD, phD, 1, gtid, e);
+        }
         if (gtid == 0)
             for (int q = 0; q < 5; ++q) a.out[5 * (size_t)d.slot + q] = e[q];
     } else {
@@ -736,16 +932,17 @@ template <typename T, int MEXP, bool SYM, int TPW>
 __global__ void __launch_bounds__(TPW) trial_kernel(PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    T *sx, *sy, *sz, *redT;
-    double *redD;
-    pass_smem<T, TPW>(smem, a.stride, sx, sy, sz, redT, redD);
+    GroupMem<T> mem;
+    mem.bind(smem, a.stride, TPW, false);
+    T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
+    double *redD = mem.redD;
     const DevWalker d = a.walkers[blockIdx.x];
     const int gtid = threadIdx.x;
     int phT = 0;
     constexpr int VN = Vec<T>::N;
     const T *gx = reinterpret_cast<const T *>(a.pos) + d.off;
     const T L = (T)d.L;
-    if (!load_walker<T, TPW>(gx, d.n, d.pad, L, sx, sy, sz, redT, phT, 1, gtid)) {
+    if (!load_walker<T, TPW>(gx, d.n, d.pad, a.stride, L, sx, sy, sz, redT, phT, 1, gtid)) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
         return;
     }
@@ -782,9 +979,10 @@ template <typename T, bool SYM, int TPW>
 __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    T *sx, *sy, *sz, *redT;
-    double *redD;
-    pass_smem<T, TPW>(smem, a.stride, sx, sy, sz, redT, redD);
+    GroupMem<T> mem;
+    mem.bind(smem, a.stride, TPW, false);
+    T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
+    double *redD = mem.redD;
     const DevWalker d = a.walkers[blockIdx.x];
     const int gtid = threadIdx.x;
     int phT = 0, phD = 0;
@@ -792,7 +990,7 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
     using V = typename Vec<T>::type;
     const T *gx = reinterpret_cast<const T *>(a.pos) + d.off;
     const T L = (T)d.L, iL = (T)1 / L, hL2 = (T)(0.25 * d.L * d.L);
-    if (!load_walker<T, TPW>(gx, d.n, d.pad, L, sx, sy, sz, redT, phT, 1, gtid)) {
+    if (!load_walker<T, TPW>(gx, d.n, d.pad, a.stride, L, sx, sy, sz, redT, phT, 1, gtid)) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
         return;
     }
