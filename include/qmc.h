@@ -56,6 +56,7 @@ extern "C" {
 #define QMC_DEVERR_NONFINITE_POS 1u   /* a loaded coordinate was NaN/Inf or outside [0, L] */
 #define QMC_DEVERR_NONFINITE_RATIO 2u /* a trial log-ratio was NaN */
 #define QMC_DEVERR_BAD_INDEX 4u       /* qmc_trial_delta: an atom index outside [0, n) (move skipped) */
+#define QMC_DEVERR_TIMEOUT 8u         /* qmc_sweep: a wait on the walker queue exceeded 10 s */
 
 /* One walker (one Markov chain).  64 bytes. */
 typedef struct qmc_walker_desc {

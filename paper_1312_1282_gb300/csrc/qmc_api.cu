@@ -63,6 +63,9 @@ struct Plan {
     int W = 0;
     DevWalker *d_walkers = nullptr;
     int *d_order = nullptr;
+    uint2 *q_slots = nullptr;  // walker FIFO of the persistent sweep
+    int *q_prog = nullptr;
+    unsigned *q_ctr = nullptr;  // head, tail
     int maxn = 0, maxpad = 0, maxsites = 0;
     bool m5 = true;
 };
@@ -199,6 +202,9 @@ void free_plan(Plan *p)
 {
     if (p->d_walkers) cudaFree(p->d_walkers);
     if (p->d_order) cudaFree(p->d_order);
+    if (p->q_slots) cudaFree(p->q_slots);
+    if (p->q_prog) cudaFree(p->q_prog);
+    if (p->q_ctr) cudaFree(p->q_ctr);
     delete p;
 }
 
@@ -244,6 +250,9 @@ int get_plan(const qmc_walker_desc *d, int W, const qmc_options *o, cudaStream_t
     }
     cudaError_t e = cudaMalloc(&p->d_walkers, sizeof(DevWalker) * (size_t)W);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int) * (size_t)W);
+    if (e == cudaSuccess) e = cudaMalloc(&p->q_slots, sizeof(uint2) * (size_t)W);
+    if (e == cudaSuccess) e = cudaMalloc(&p->q_prog, sizeof(int) * (size_t)W);
+    if (e == cudaSuccess) e = cudaMalloc(&p->q_ctr, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_walkers, host.data(), sizeof(DevWalker) * (size_t)W, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_order, order.data(), sizeof(int) * (size_t)W, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -316,6 +325,15 @@ int check_ptr(const void *p, const char *name, size_t align)
     return QMC_OK;
 }
 
+cudaError_t sweep_occupancy(int precision, int tpw, Variant v, int block, size_t smem, int *ctas)
+{
+    if (precision == QMC_FP64)
+        return tpw <= 128 ? occupancy_sweep_f64_small(tpw, v, block, smem, ctas)
+                          : occupancy_sweep_f64_big(tpw, v, block, smem, ctas);
+    return tpw <= 128 ? occupancy_sweep_f32_small(tpw, v, block, smem, ctas)
+                      : occupancy_sweep_f32_big(tpw, v, block, smem, ctas);
+}
+
 cudaError_t launch_sweep(int precision, int tpw, Variant v, int grid, int block, size_t smem, cudaStream_t st,
                          const SweepArgs &a)
 {
@@ -379,9 +397,41 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     a.sequential = o->sequential;
     a.h2m = o->hbar2_over_m;
     a.err = p.ds->err;
-    const int grid = (W + G - 1) / G;
+    a.dynamic = 0;
+    a.chunk_moves = 0;
+    a.q_total = 0;
+    a.q_head = a.q_tail = nullptr;
+    a.q_slots = nullptr;
+    a.q_prog = nullptr;
+    int grid = (W + G - 1) / G;
     const size_t smem = (size_t)G * smem_group(o->precision, P.maxpad, tpw, a.tile != 0);
-    cudaError_t e = launch_sweep(o->precision, tpw, variant_of(P, o), grid, G * tpw, smem, st, a);
+    const Variant v = variant_of(P, o);
+    cudaError_t e;
+    if (W > p.ds->nsm) {
+        // persistent mode: every resident CTA slot takes ready walkers in chunks of about a quarter
+        // sweep of the largest walker, so that SMs stay evenly loaded when W is not a multiple of
+        // the SM count
+        int ctas = 0;
+        e = sweep_occupancy(o->precision, tpw, v, G * tpw, smem, &ctas);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        const long long chunk = std::max(32, ((P.maxn + 3) / 4 + 31) / 32 * 32);
+        long long total = 0;
+        for (int w = 0; w < W; ++w) total += ((long long)nsweeps * d[w].n + chunk - 1) / chunk;
+        if (ctas > 0 && total < (1ll << 31)) {
+            a.dynamic = 1;
+            a.chunk_moves = (int)chunk;
+            a.q_total = (unsigned)total;
+            a.q_head = P.q_ctr;
+            a.q_tail = P.q_ctr + 1;
+            a.q_slots = P.q_slots;
+            a.q_prog = P.q_prog;
+            grid = ctas * p.ds->nsm;
+            e = launch_queue_init(P.d_order, W, P.q_slots, P.q_prog, P.q_ctr, P.q_ctr + 1, st);
+            if (e != cudaSuccess) return cuda_fail(e, "walker queue init");
+            g_launches.fetch_add(1);
+        }
+    }
+    e = launch_sweep(o->precision, tpw, v, grid, G * tpw, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
     g_launches.fetch_add(1);
     return QMC_OK;
@@ -566,9 +616,10 @@ int qmc_status(void *stream, int timeout_ms, uint32_t *bits)
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
     if (bits) *bits = h;
     if (h)
-        return fail(QMC_ERR_DEVICE, "kernel flagged %s%s%s", (h & QMC_DEVERR_NONFINITE_POS) ? "[bad coordinate]" : "",
+        return fail(QMC_ERR_DEVICE, "kernel flagged %s%s%s%s", (h & QMC_DEVERR_NONFINITE_POS) ? "[bad coordinate]" : "",
                     (h & QMC_DEVERR_NONFINITE_RATIO) ? "[non-finite ratio]" : "",
-                    (h & QMC_DEVERR_BAD_INDEX) ? "[atom index out of range]" : "");
+                    (h & QMC_DEVERR_BAD_INDEX) ? "[atom index out of range]" : "",
+                    (h & QMC_DEVERR_TIMEOUT) ? "[walker queue wait timed out]" : "");
     return QMC_OK;
 }
 
@@ -735,6 +786,12 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     a.sequential = opt->sequential;
     a.h2m = opt->hbar2_over_m;
     a.err = err ? reinterpret_cast<unsigned *>(err) : d_err;
+    a.dynamic = 0;  // one walker per group: no queue memory needed
+    a.chunk_moves = 0;
+    a.q_total = 0;
+    a.q_head = a.q_tail = nullptr;
+    a.q_slots = nullptr;
+    a.q_prog = nullptr;
     const int grid = (W + G - 1) / G;
     const size_t smem = (size_t)G * smem_group(opt->precision, P.maxpad, tpw, a.tile != 0);
     e = launch_sweep(opt->precision, tpw, variant_of(P, opt), grid, G * tpw, smem, st, a);

@@ -85,4 +85,25 @@ cudaError_t launch_init(int precision, int grid, size_t smem, cudaStream_t st, c
     return cudaGetLastError();
 }
 
+// fills the FIFO with the walkers in processing order and clears the chunk counters
+__global__ void queue_init_kernel(const int *order, int W, uint2 *slots, int *prog, unsigned *head, unsigned *tail)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < W) {
+        slots[i] = make_uint2((unsigned)i + 1u, (unsigned)order[i]);
+        prog[order[i]] = 0;
+    }
+    if (i == 0) {
+        *head = 0u;
+        *tail = (unsigned)W;
+    }
+}
+
+cudaError_t launch_queue_init(const int *order, int W, uint2 *slots, int *prog, unsigned *head, unsigned *tail,
+                              cudaStream_t st)
+{
+    queue_init_kernel<<<(W + 255) / 256, 256, 0, st>>>(order, W, slots, prog, head, tail);
+    return cudaGetLastError();
+}
+
 }  // namespace qmc

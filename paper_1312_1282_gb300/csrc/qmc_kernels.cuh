@@ -14,6 +14,7 @@
 // the last accepted move, so a move needs exactly one group barrier (none for TPW = 32).
 #pragma once
 
+#include <cuda/atomic>
 #include <type_traits>
 
 #include "qmc_device.cuh"
@@ -67,6 +68,13 @@ struct SweepArgs {
     int proposal, sequential;
     double h2m;
     unsigned *err;
+    // persistent mode: walkers circulate through a FIFO of ready walkers in chunks of moves
+    int dynamic;             // 0: one walker per thread group for the whole call
+    int chunk_moves;         // moves per chunk (a multiple of 32)
+    unsigned q_total;        // chunks of all walkers: sum over w of ceil(nsweeps n_w / chunk_moves)
+    unsigned *q_head, *q_tail;
+    uint2 *q_slots;          // [W] {sequence, walker table index}
+    int *q_prog;             // [W] chunks done (bit 30: walker faulted, its chunks are skipped)
 };
 
 // Moves per batch of the sweep: the partner loop serves KB trial moves at once and the group
@@ -83,7 +91,7 @@ constexpr int KB = QMC_KB;
 // a batch (2 phases of KB x KB T's), and with the tiled energy pass the drift components
 // Fx | Fy | Fz (stride floats each).
 struct GroupLayout {
-    size_t red, redT, dsm, F, bytes;
+    size_t red, redT, dsm, bc, F, bytes;
 };
 template <typename T> __host__ __device__ constexpr GroupLayout group_layout(int stride, int tpw, bool tile)
 {
@@ -91,7 +99,8 @@ template <typename T> __host__ __device__ constexpr GroupLayout group_layout(int
     g.red = (size_t)3 * stride * sizeof(T);
     g.redT = g.red + (size_t)2 * (tpw / 32) * sizeof(double);
     g.dsm = g.redT + (size_t)2 * KB * (tpw / 32) * sizeof(T);
-    g.F = (g.dsm + (size_t)2 * KB * KB * sizeof(T) + 15) / 16 * 16;
+    g.bc = (g.dsm + (size_t)2 * KB * KB * sizeof(T) + 15) / 16 * 16;
+    g.F = g.bc + 16;
     g.bytes = g.F + (tile ? (size_t)3 * stride * sizeof(float) : 0);
     return g;
 }
@@ -105,9 +114,11 @@ template <typename T> struct GroupMem {
     T *sx, *sy, *sz, *redT, *dsm;
     double *redD;
     float *fx, *fy, *fz;
+    int *bc;  // one int broadcast from the group's thread 0
     __device__ __forceinline__ void bind(unsigned char *base, int stride, int tpw, bool tile)
     {
         const GroupLayout g = group_layout<T>(stride, tpw, tile);
+        bc = reinterpret_cast<int *>(base + g.bc);
         sx = reinterpret_cast<T *>(base);
         sy = sx + stride;
         sz = sy + stride;
@@ -705,10 +716,15 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
 }
 
 // ----------------------------------------------------------------------------------------------
-// The sweep: one group runs one walker's chain for a whole call.
+// The sweep: one group advances one walker through moves [m_begin, m_end) of the call (move m is
+// move m mod n of sweep k0 + m / n), doing the after-sweep work (ln psi recompute, energy sample)
+// at every sweep it completes.  The walker is loaded from HBM at the start and written back at the
+// end; `last` marks the range that ends the call (the walker's sweep counter advances then).
+// Returns false if the walker faulted (nothing of it is written back).
 // ----------------------------------------------------------------------------------------------
 template <typename T, int MEXP, bool SYM, int TPW>
-__device__ void run_walker(const SweepArgs &a, const DevWalker &d, const GroupMem<T> &mem, int gtid, int bar_id)
+__device__ bool run_range(const SweepArgs &a, const DevWalker &d, const GroupMem<T> &mem, int gtid, int bar_id,
+                          long long m_begin, long long m_end, bool last)
 {
     T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
     double *redD = mem.redD;
@@ -721,7 +737,7 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, const GroupMe
 
     if (!load_walker<T, TPW>(gx, n, pad, a.stride, L, sx, sy, sz, redT, phT, bar_id, gtid)) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
-        return;
+        return false;
     }
     Jas<T, MEXP, SYM> J;
     J.init(d);
@@ -736,10 +752,14 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, const GroupMe
     const uint32_t wid = d.wid;
     T *dsm = mem.dsm;  // cross terms of a batch
 
-    for (int it = 0; it < a.nsweeps; ++it) {
+    for (long long m = m_begin; m < m_end;) {
+        const long long it = m / n;
+        const int t_start = (int)(m - it * n);
+        const int t_stop = (int)min((long long)n, (long long)t_start + (m_end - m));
+        m += t_stop - t_start;
         const unsigned long long kk = k0 + (unsigned long long)it;
         const uint32_t k = (uint32_t)kk;
-        for (int t0 = 0; t0 < n; t0 += 32) {
+        for (int t0 = t_start & ~31; t0 < t_stop; t0 += 32) {
             // random numbers of moves t0 .. t0+31, one move per lane (Sec. 5.2: 5 numbers per move)
             const uint32_t t = (uint32_t)(t0 + lane);
             const uint4 rw = philox(t, k, wid, ST_STEP, a.seed);
@@ -768,8 +788,8 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, const GroupMe
             }
             // FP32: the decision is taken as 2 Delta > ln xi, with ln xi computed here once per move
             if constexpr (std::is_same<T, float>::value) mxi = logf(mxi);
-            const int cnt = min(32, n - t0);
-            int tt = 0;
+            const int cnt = min(32, t_stop - t0);
+            int tt = max(0, t_start - t0);
             for (; tt + KB <= cnt; tt += KB) {
                 int bs[KB];
                 T bdx[KB], bdy[KB], bdz[KB], bxi[KB];
@@ -800,7 +820,7 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, const GroupMe
                 }
                 if (!ok) {
                     if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
-                    return;
+                    return false;
                 }
             }
             for (; tt < cnt; ++tt) {
@@ -810,10 +830,11 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, const GroupMe
                 if (!move_batch<T, MEXP, SYM, TPW, 1, KB>(J, sx, sy, sz, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
                                                           dsm, phT, bar_id, gtid)) {
                     if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
-                    return;
+                    return false;
                 }
             }
         }
+        if (t_stop < n) break;  // the range ends inside this sweep
         group_sync<TPW>(bar_id);
         rec.clear();
         if (a.recompute_every > 0 && (kk + 1) % (unsigned long long)a.recompute_every == 0)
@@ -846,9 +867,62 @@ __device__ void run_walker(const SweepArgs &a, const DevWalker &d, const GroupMe
     if (gtid == 0) {
         A[7] += (double)nacc;  // integer-valued: exact in any order
         a.logpsi[slot] = lp;
-        a.sweep[slot] = k0 + (unsigned long long)a.nsweeps;
+        if (last) a.sweep[slot] = k0 + (unsigned long long)a.nsweeps;
     }
+    return true;
 }
+
+// ----------------------------------------------------------------------------------------------
+// FIFO of ready walkers (persistent mode).  A bounded multi-producer multi-consumer ring with a
+// sequence number per slot: the pop of ticket p waits for sequence p + 1, takes the walker and
+// frees the slot (sequence p + W); the push of ticket p waits for sequence p, stores the walker
+// and publishes it (sequence p + 1).  It starts full (all W walkers) and exactly W walkers
+// circulate, so a push finds its slot free as soon as the matching pop has left it.  Every wait
+// is bounded (10 s of global time); on expiry the error word gets QMC_DEVERR_TIMEOUT.
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool wait_seq(unsigned *seq_word, unsigned want, unsigned *err)
+{
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> seq(*seq_word);
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0; it < (1u << 30); ++it) {
+        if (seq.load(cuda::memory_order_acquire) == want) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > 10000000000ull) break;
+        __nanosleep(128);
+    }
+    atomicOr(err, QMC_DEVERR_TIMEOUT);
+    return false;
+}
+
+// next walker table index, or -1 when all chunks have been handed out (or on a timeout)
+__device__ __forceinline__ int queue_pop(const SweepArgs &a, unsigned total)
+{
+    const unsigned pos = atomicAdd(a.q_head, 1u);
+    if (pos >= total) return -1;
+    uint2 *sl = a.q_slots + pos % (unsigned)a.W;
+    if (!wait_seq(&sl->x, pos + 1, a.err)) return -1;
+    const int w = (int)*reinterpret_cast<volatile unsigned *>(&sl->y);
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device>(sl->x).store(pos + (unsigned)a.W,
+                                                                       cuda::memory_order_release);
+    return w;
+}
+
+__device__ __forceinline__ void queue_push(const SweepArgs &a, int w)
+{
+    const unsigned pos = atomicAdd(a.q_tail, 1u);
+    uint2 *sl = a.q_slots + pos % (unsigned)a.W;
+    if (!wait_seq(&sl->x, pos, a.err)) return;
+    *reinterpret_cast<volatile unsigned *>(&sl->y) = (unsigned)w;
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device>(sl->x).store(pos + 1, cuda::memory_order_release);
+}
+
+
 
 // CTAs hold up to 256 threads (TPW <= 256) or exactly one group; at least 1024 resident threads
 // per SM, i.e. at most 64 registers per thread.
@@ -862,11 +936,39 @@ __global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_ker
     extern __shared__ __align__(16) unsigned char smem[];
     const int g = threadIdx.x / TPW, gtid = threadIdx.x % TPW;
     const int item = blockIdx.x * a.G + g;
-    if (item >= a.W) return;  // only group barriers follow, so whole groups may leave
+    if (!a.dynamic && item >= a.W) return;  // only group barriers follow, so whole groups may leave
     GroupMem<T> mem;
     mem.bind(smem + (size_t)g * group_smem<T>(a.stride, TPW, a.tile), a.stride, TPW, a.tile);
-    const DevWalker d = a.walkers[a.order[item]];
-    run_walker<T, MEXP, SYM, TPW>(a, d, mem, gtid, 1 + g);
+    if (!a.dynamic) {
+        const DevWalker d = a.walkers[a.order[item]];
+        run_range<T, MEXP, SYM, TPW>(a, d, mem, gtid, 1 + g, 0, (long long)a.nsweeps * d.n, true);
+        return;
+    }
+    // persistent: take ready walkers from the FIFO, advance each by one chunk, put it back
+    constexpr int DEAD = 1 << 30;
+    for (;;) {
+        if (gtid == 0) *mem.bc = queue_pop(a, a.q_total);
+        group_sync<TPW>(1 + g);
+        const int w = *mem.bc;
+        group_sync<TPW>(1 + g);
+        if (w < 0) return;
+        // the walker was last written by another SM: acquire its state (positions, ln psi, sums)
+        cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
+        const DevWalker d = a.walkers[w];
+        const long long total = (long long)a.nsweeps * d.n;
+        const int c = a.q_prog[w];
+        const long long m0 = (long long)(c & (DEAD - 1)) * a.chunk_moves;
+        const long long m1 = min(total, m0 + a.chunk_moves);
+        bool ok = true;
+        if (!(c & DEAD)) ok = run_range<T, MEXP, SYM, TPW>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total);
+        __threadfence();  // this thread's stores of the walker state, before it is handed on
+        group_sync<TPW>(1 + g);
+        if (gtid == 0) {
+            a.q_prog[w] = (c + 1) | (ok ? 0 : DEAD);
+            __threadfence();
+            if (m1 < total) queue_push(a, w);
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------------------------

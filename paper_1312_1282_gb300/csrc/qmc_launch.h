@@ -22,6 +22,14 @@ cudaError_t launch_sweep_f64_small(int tpw, Variant v, int grid, int block, size
 cudaError_t launch_sweep_f64_big(int tpw, Variant v, int grid, int block, size_t smem, cudaStream_t st,
                                  const SweepArgs &a);
 
+// resident CTAs per SM of a sweep kernel instantiation with this block and shared memory
+cudaError_t occupancy_sweep_f32_small(int tpw, Variant v, int block, size_t smem, int *ctas);
+cudaError_t occupancy_sweep_f32_big(int tpw, Variant v, int block, size_t smem, int *ctas);
+cudaError_t occupancy_sweep_f64_small(int tpw, Variant v, int block, size_t smem, int *ctas);
+cudaError_t occupancy_sweep_f64_big(int tpw, Variant v, int block, size_t smem, int *ctas);
+cudaError_t launch_queue_init(const int *order, int W, uint2 *slots, int *prog, unsigned *head, unsigned *tail,
+                              cudaStream_t st);
+
 constexpr int PASS_TPW = 256;   // threads per walker of the stand-alone passes
 constexpr int TRIAL_TPW = 128;  // threads per walker of qmc_trial_delta
 

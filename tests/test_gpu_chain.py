@@ -175,3 +175,49 @@ def test_full_size_sampled_walkers():
         e = oracle.local_energy(blk1, L, qi.B_HE, 5.0, 1, H2M)
         assert np.all(np.abs(a[w, [2, 3, 4, 5, 0]] - e) <= 1e-5 * energy_scale(e))
     assert matched >= 2
+
+
+def test_persistent_queue_mode_matches_oracle_and_static_path():
+    """More walkers than SMs: qmc_sweep runs persistent CTAs that take walkers from a FIFO in
+    chunks of moves.  The chains must be those of the oracle (FP64, bit for bit) and of the
+    one-walker-per-group path of qmc_sweep_static, for an uneven batch."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    W = nsm + 37
+    ns = [64, 130, 200, 97] * (W // 4) + [64] * (W % 4)
+    A = lattice_batch(ns, q.QMC_FP64, seed=8)
+    B = lattice_batch(ns, q.QMC_FP64, seed=8)
+    opt = q.options(precision=q.QMC_FP64, recompute_every=3)
+    la, sa, aa = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lb, sb, ab = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    q.qmc_log_psi(A.d, opt, A.pos, la)
+    q.qmc_log_psi(B.d, opt, B.pos, lb)
+    q.qmc_sweep(A.d, opt, A.pos, la, sa, 0xD1CE, 4, 2, aa)
+    q.qmc_sweep(A.d, opt, A.pos, la, sa, 0xD1CE, 3, 2, aa)
+    q.qmc_sweep_static(B.d, opt, B.pos, lb, sb, 0xD1CE, 7, 2, ab)
+    assert q.qmc_status(timeout_ms=120000) == 0
+    assert torch.equal(A.pos, B.pos) and torch.equal(sa, sb)
+    np.testing.assert_allclose(la.cpu().numpy(), lb.cpu().numpy(), rtol=1e-12)
+    np.testing.assert_allclose(aa.cpu().numpy(), ab.cpu().numpy(), rtol=1e-12)
+    acc = aa.cpu().numpy()
+    for w in (0, 1, 2, 3, W - 1):
+        pos, olp, ok, oacc, _ = _oracle_chain(A, w, 0xD1CE, 7, 2, opt)
+        assert np.array_equal(A.positions(w), pos)
+        assert acc[w, 7] == oacc[7] and acc[w, 6] == oacc[6]
+        np.testing.assert_allclose(acc[w, :6], oacc[:6], rtol=1e-10, atol=1e-9)
+
+
+def test_persistent_queue_mode_survives_a_faulted_walker():
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    W = nsm + 5
+    P = lattice_batch([64] * W, q.QMC_FP32, seed=9)
+    before = P.pos.clone()
+    bad = P.d[3]
+    P.pos[bad.offset + 7] = float("nan")
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    q.qmc_sweep(P.d, q.options(), P.pos, lp, sw, 4, 6, 3, acc)
+    with pytest.raises(q.QmcError, match="bad coordinate"):
+        q.qmc_status(timeout_ms=120000)
+    s = sw.cpu().numpy()
+    assert s[3] == 0 and np.all(np.delete(s, 3) == 6)
+    host = P.pos.cpu()
+    assert torch.equal(host[bad.offset + 8:bad.offset + 3 * 64], before[bad.offset + 8:bad.offset + 3 * 64].cpu())
