@@ -1,0 +1,133 @@
+"""Statistical checks of the GPU chains: averages, not single configurations.
+
+- The paper's sample run (Sec. 5.4): E/N of liquid 4He at 1000 atoms, b = 3.07 A, Gaussian
+  displacements of RMS 0.5 rho^(-1/3) (Sec. 7).
+- The three kinetic estimators agree in expectation (integration by parts, symmetrised u).
+- FP32 and FP64 chains of the same streams agree on E/N within the combined 2 sigma.
+- FP32 GPU vs the FP64 oracle, both run from the same start on the small workload
+  (N = 64, one walker, cube step 0.8 A), agree within 2 sigma (block averages).
+- The Hamiltonian is Hermitian, so <dE_L/db> = 0 within 2 sigma.
+Error bars: spread across independent walkers, or blocking for a single chain (Eq. CorrelatedError).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1312_1282_gb300 as q
+import qmc_inputs as qi
+from tests._gpu import H2M, zeros
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_sample_run.txt")
+
+
+def _batch(n, W, precision, step, proposal=q.QMC_CUBE, b=qi.B_HE, seed=1, id0=0):
+    L = qi.box_side(n, qi.RHO_HE)
+    pad = qi.pad4(n)
+    d = q.descs([(n, pad, w * 3 * pad, id0 + w, L, 0.0, b, 5.0, step) for w in range(W)])
+    opt = q.options(precision=precision, proposal=proposal, recompute_every=50)
+    dt = torch.float64 if precision == q.QMC_FP64 else torch.float32
+    pos = torch.empty(W * 3 * pad, dtype=dt, device="cuda")
+    q.qmc_init_walkers(d, seed, 0.1, opt, pos)
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    q.qmc_log_psi(d, opt, pos, lp)
+    return d, opt, pos, lp, sw, acc
+
+
+def _per_walker(acc, n):
+    a = acc.cpu().numpy()
+    ns = a[:, 6]
+    return {"E": a[:, 0] / ns / n, "V": a[:, 2] / ns / n, "TL": a[:, 3] / ns / n, "TPB": a[:, 4] / ns / n,
+            "TF": a[:, 5] / ns / n, "acc": a[:, 7]}
+
+
+def _mean_err(x):
+    return float(np.mean(x)), float(np.std(x, ddof=1) / math.sqrt(len(x)))
+
+
+def test_paper_sample_run_energy_and_estimators():
+    rows = np.array([[float(v) for v in ln.split()] for ln in open(GOLD) if ln.strip() and ln[0] != "#"])
+    e_ref = rows[:, 1].mean()
+    n, W = 1000, 64
+    sigma = 0.5 * qi.RHO_HE ** (-1 / 3) / math.sqrt(3)  # RMS of the displacement vector
+    d, opt, pos, lp, sw, acc = _batch(n, W, q.QMC_FP32, sigma, proposal=q.QMC_GAUSS, seed=0x5A3)
+    q.qmc_sweep(d, opt, pos, lp, sw, 0x5A3, 300, 0, acc)
+    acc.zero_()
+    q.qmc_sweep(d, opt, pos, lp, sw, 0x5A3, 1200, 4, acc)
+    assert q.qmc_status(timeout_ms=600000) == 0
+    r = _per_walker(acc, n)
+    e, de = _mean_err(r["E"])
+    # the paper's number is for its own (unprinted) stream and step multiplier: a loose pin
+    assert abs(e - e_ref) < 3 * de + 0.03, (e, de, e_ref)
+    for k in ("TL", "TF"):
+        dk, ek = _mean_err(r[k] - r["TPB"])
+        assert abs(dk) < 3 * ek, (k, dk, ek)
+    # Sec. 7 quotes about 40 % (the sample run 37 %) for an RMS step of 0.5 rho^(-1/3); read as
+    # the RMS of the displacement vector this step accepts about 29 % here, and as the RMS per
+    # component about 12 %: the paper's step multiplier is not printed, so only the range is pinned
+    rate = r["acc"].sum() / (W * n * 1200)
+    assert 0.2 < rate < 0.45, rate
+
+
+def test_fp32_and_fp64_chains_agree():
+    n, W, step = 512, 256, 0.8
+    res = {}
+    for prec in (q.QMC_FP64, q.QMC_FP32):
+        d, opt, pos, lp, sw, acc = _batch(n, W, prec, step, seed=0x5EED0002)
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0002, 100, 0, acc)
+        acc.zero_()
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0002, 400, 5, acc)
+        assert q.qmc_status(timeout_ms=600000) == 0
+        res[prec] = _per_walker(acc, n)["E"]
+    diff = res[q.QMC_FP32] - res[q.QMC_FP64]
+    m, e = _mean_err(diff)
+    e32, s32 = _mean_err(res[q.QMC_FP32])
+    e64, s64 = _mean_err(res[q.QMC_FP64])
+    assert abs(e32 - e64) < 2 * math.hypot(s32, s64)
+    assert abs(m) < 3 * e + 1e-9
+
+
+def test_fp32_gpu_matches_fp64_oracle_small_workload():
+    """N = 64, one walker, cube step 0.8 A: 1000 + 2000 sweeps, E_L every sweep."""
+    n = 64
+    L = qi.box_side(n, qi.RHO_HE)
+    d, opt, pos, lp, sw, acc = _batch(n, 1, q.QMC_FP32, 0.8, seed=0x5EED0001)
+    start = pos.cpu().numpy().astype(np.float64).reshape(3, -1)[:, :n]
+    q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0001, 1000, 0, acc)
+    blocks_gpu = []
+    for _ in range(20):
+        acc.zero_()
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0001, 100, 1, acc)
+        a = acc.cpu().numpy()[0]
+        blocks_gpu.append(a[0] / a[6] / n)
+    P = oracle.make_walker(n, L, qi.B_HE, 5.0, 0.8, seed=0x5EED0001, wid=0, hbar2_over_m=H2M, recompute_every=50)
+    opos, olp, k, _, _ = oracle.run_walker(P, start, oracle.log_psi(start, L, qi.B_HE), 0, 1000, 0)
+    blocks_orc = []
+    for _ in range(20):
+        opos, olp, k, oa, _ = oracle.run_walker(P, opos, olp, k, 100, 1)
+        blocks_orc.append(oa[0] / oa[6] / n)
+    g, eg = _mean_err(np.array(blocks_gpu))
+    o, eo = _mean_err(np.array(blocks_orc))
+    assert abs(g - o) < 2.5 * math.hypot(eg, eo), (g, eg, o, eo)
+
+
+def test_energy_derivative_has_zero_mean():
+    n, W = 64, 512
+    d, opt, pos, lp, sw, acc = _batch(n, W, q.QMC_FP32, 0.8, seed=0x5EED0005)
+    q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, 300, 0, acc)
+    samples = []
+    for _ in range(8):
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, 10, 0, acc)
+        out = zeros((W, 6))
+        q.qmc_energy_grad(d, opt, pos, out)
+        samples.append(out.cpu().numpy())
+    s = np.concatenate(samples)
+    for col in (4, 5):  # dE_L/db, dE_L/dm
+        m, e = _mean_err(s[:, col])
+        assert abs(m) < 3 * e, (col, m, e)
+    # O_b = d ln psi / db = (m/b) ln psi (u is linear in b^m)
+    np.testing.assert_allclose(s[:, 2], 5.0 / qi.B_HE * s[:, 0], rtol=1e-6)
