@@ -37,11 +37,11 @@ import qmc_inputs as qi  # noqa: E402
 N_ATOMS, WALKERS, SWEEPS_PER_STEP = 1952, 528, 5
 METRIC = "pair evals/s and sweeps/s at N=1952, FP32-batched vs FP64 plain, E/atom within 2σ"
 WORKLOAD = "VMC liquid 4He N=1952 rho=0.02186 b=3.07 m=5 Aziz-II, 528 walkers, 5 sweeps + 1 local energy per step"
-# FP32 pipe operations per pair evaluation of the move kernel (min-image distance 9 + r^2 3,
-# u with 5th powers 11, old/new difference and accumulation 1.5 -- counted in the design doc) and per
-# directed pair of the local-energy pass.
-C_PAIR = 25.0
-C_ENERGY = 64.0
+# FP32 operations per pair evaluation of a move (difference 3, image fold 6, r^2 3, clamp 1,
+# r and L - r 2, fifth powers 6, u 2, accumulation 1) and per unordered pair of the local-energy
+# pass (71); the op lists are in the design doc.  SFU operations (2 and 3-4) are not counted.
+C_PAIR = 24.0
+C_ENERGY = 71.0
 FP32_LANES_PER_SM = 128
 
 
@@ -274,7 +274,7 @@ def run_native(args):
     pe_step = pair_evals_per_sweep(n) * W * SWEEPS_PER_STEP
     value = pe_step * world * args.steps / (total_ms * 1e-3)
     sweeps_per_s = W * world * SWEEPS_PER_STEP * args.steps / (total_ms * 1e-3)
-    energy_pairs = float(n) * (n - 1) * W  # directed pairs of one local-energy pass per walker
+    energy_pairs = float(n) * (n - 1) / 2 * W  # unordered pairs of one local-energy pass per walker
 
     # ---- FP64 plain single-walker path (same kernel in double, one walker) ----
     opt64 = q.options(precision=q.QMC_FP64, recompute_every=50)
