@@ -371,6 +371,167 @@ def run_native(args):
     return 0
 
 
+# ---------------------------------------------------------------------------------------------
+# other workloads (not the headline line): uneven batch, large N with gradients, FP32 vs FP64
+# ---------------------------------------------------------------------------------------------
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_uneven(args):
+    """Walker groups (N, W) = (128, 2048), (500, 1024), (1000, 512), (1952, 256), (4000, 128);
+    per-walker density U[0.0197, 0.0262] and b U[2.9, 3.2]; cube step 0.3 rho^(-1/3); one step =
+    5 sweeps + 1 energy sample of all 3968 walkers in one persistent launch, replayed as a CUDA graph."""
+    import torch
+    import paper_1312_1282_gb300 as q
+    torch.cuda.set_device(0)
+    params = qi.uneven_params(qi.uneven_groups(), seed=0x5EED0004)
+    rows, off = [], 0
+    for w, (n, rho, b) in enumerate(params):
+        pad = qi.pad4(n)
+        L = qi.box_side(n, rho)
+        rows.append((n, pad, off, w, L, 0.0, b, 5.0, 0.3 * rho ** (-1.0 / 3.0)))
+        off += 3 * pad
+    d = q.descs(rows)
+    W = len(rows)
+    opt = q.options(precision=q.QMC_FP32, recompute_every=50)
+    pos = torch.empty(off, dtype=torch.float32, device="cuda")
+    lp = torch.zeros(W, dtype=torch.float64, device="cuda")
+    sw = torch.zeros(W, dtype=torch.int64, device="cuda")
+    acc = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+    q.qmc_init_walkers(d, 0x5EED0004, 0.1, opt, pos)
+    q.qmc_log_psi(d, opt, pos, lp)
+    tpw = q.qmc_autotune(d, opt, pos)
+    q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0004, args.equil, 0, acc)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0004, SWEEPS_PER_STEP, SWEEPS_PER_STEP, acc, stream)  # warm
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0004, SWEEPS_PER_STEP, SWEEPS_PER_STEP, acc, stream)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    acc.zero_()
+    k0 = sw.clone()
+    a, b = _events(torch)
+    a.record()
+    for _ in range(args.steps):
+        graph.replay()
+    b.record()
+    torch.cuda.synchronize()
+    q.qmc_status(None, 600000)
+    ms = a.elapsed_time(b) / args.steps
+    assert torch.all(sw - k0 == SWEEPS_PER_STEP * args.steps), "graph replays must advance the sweep counters"
+    pe = sum(2.0 * r[0] * (r[0] - 1) for r in rows) * SWEEPS_PER_STEP
+    a_np = acc.cpu().numpy()
+    groups = {}
+    for r, row in zip(a_np, rows):
+        groups.setdefault(row[0], []).append(r[0] / r[6] / row[0])
+    print(json.dumps({"config": "uneven batch, one persistent launch per step, CUDA graph replay",
+                      "walkers": W, "threads_per_walker": tpw, "ms_per_step": ms, "pair_evals_per_s": pe / (ms * 1e-3),
+                      "E_per_atom_by_N": {str(k): float(np.mean(v)) for k, v in sorted(groups.items())}}), flush=True)
+    return 0
+
+
+def run_large(args):
+    """N = 10000 at 0.02186 A^-3, one walker per SM, FP32; a step = 20 sweeps then the adjoint
+    (ln psi, E_L and their (b, m) derivatives) of every walker."""
+    import torch
+    import paper_1312_1282_gb300 as q
+    torch.cuda.set_device(0)
+    n = 10000
+    W = torch.cuda.get_device_properties(0).multi_processor_count
+    L = qi.box_side(n, qi.RHO_HE)
+    pad = qi.pad4(n)
+    d = q.descs([(n, pad, w * 3 * pad, w, L, 0.0, qi.B_HE, 5.0, 0.8) for w in range(W)])
+    opt = q.options(precision=q.QMC_FP32, recompute_every=50)
+    pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
+    lp = torch.zeros(W, dtype=torch.float64, device="cuda")
+    sw = torch.zeros(W, dtype=torch.int64, device="cuda")
+    acc = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+    grad = torch.zeros(W, 6, dtype=torch.float64, device="cuda")
+    q.qmc_init_walkers(d, 0x5EED0005, 0.1, opt, pos)
+    q.qmc_log_psi(d, opt, pos, lp)
+    tpw = q.qmc_autotune(d, opt, pos)
+    q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, args.equil, 0, acc)
+    acc.zero_()
+    for _ in range(args.warmup):
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, 1, 0, acc)
+    torch.cuda.synchronize()
+    t_sw, t_gr = 0.0, 0.0
+    grads = []
+    for _ in range(args.steps):
+        a, b = _events(torch)
+        c, e = _events(torch)
+        a.record()
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, 20, 20, acc)
+        b.record()
+        c.record()
+        q.qmc_energy_grad(d, opt, pos, grad)
+        e.record()
+        torch.cuda.synchronize()
+        t_sw += a.elapsed_time(b)
+        t_gr += c.elapsed_time(e)
+        grads.append(grad.cpu().numpy().copy())
+    q.qmc_status(None, 600000)
+    g = np.concatenate(grads)
+    EL, Ob, Om = g[:, 1], g[:, 2], g[:, 3]
+    dE_db = 2 * (np.mean(EL * Ob) - EL.mean() * Ob.mean()) / n
+    dE_dm = 2 * (np.mean(EL * Om) - EL.mean() * Om.mean()) / n
+    pe = 2.0 * n * (n - 1) * W * 20 * args.steps
+    print(json.dumps({"config": "N=10000, one walker per SM, 20 sweeps + adjoint per step", "walkers": W,
+                      "threads_per_walker": tpw, "pair_evals_per_s": pe / (t_sw * 1e-3),
+                      "ms_per_20_sweeps": t_sw / args.steps, "ms_per_adjoint": t_gr / args.steps,
+                      "E_per_atom": float(acc[:, 0].sum() / acc[:, 6].sum() / n),
+                      "dE_per_atom_db_K_per_A": dE_db, "dE_per_atom_dm": dE_dm}), flush=True)
+    return 0
+
+
+def run_fp64cmp(args):
+    """N = 512, 1024 walkers, cube step 0.8 A: 500 + 2000 sweeps, E_L every 5, in FP32 and in FP64
+    with the same streams; E/N of both, their difference and the combined 2 sigma."""
+    import torch
+    import paper_1312_1282_gb300 as q
+    torch.cuda.set_device(0)
+    n, W = 512, 1024
+    L = qi.box_side(n, qi.RHO_HE)
+    pad = qi.pad4(n)
+    d = q.descs([(n, pad, w * 3 * pad, w, L, 0.0, qi.B_HE, 5.0, 0.8) for w in range(W)])
+    out = {}
+    for name, prec, dt in (("fp32", q.QMC_FP32, torch.float32), ("fp64", q.QMC_FP64, torch.float64)):
+        opt = q.options(precision=prec, recompute_every=50)
+        pos = torch.empty(W * 3 * pad, dtype=dt, device="cuda")
+        lp = torch.zeros(W, dtype=torch.float64, device="cuda")
+        sw = torch.zeros(W, dtype=torch.int64, device="cuda")
+        acc = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+        q.qmc_init_walkers(d, 0x5EED0002, 0.1, opt, pos)
+        q.qmc_log_psi(d, opt, pos, lp)
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0002, 500, 0, acc)
+        acc.zero_()
+        a, b = _events(torch)
+        a.record()
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0002, 2000, 5, acc)
+        b.record()
+        torch.cuda.synchronize()
+        q.qmc_status(None, 0)
+        e = (acc[:, 0] / acc[:, 6] / n).cpu().numpy()
+        out[name] = {"E": float(e.mean()), "err": float(e.std(ddof=1) / math.sqrt(W)), "ms": a.elapsed_time(b),
+                     "pair_evals_per_s": 2.0 * n * (n - 1) * W * 2000 / (a.elapsed_time(b) * 1e-3),
+                     "walker_E": e}
+    diff = out["fp32"]["walker_E"] - out["fp64"]["walker_E"]
+    res = {"config": "N=512, 1024 walkers, 500 + 2000 sweeps, E_L every 5, FP32 vs FP64",
+           "fp32": {k: v for k, v in out["fp32"].items() if k != "walker_E"},
+           "fp64": {k: v for k, v in out["fp64"].items() if k != "walker_E"},
+           "diff_mK": 1e3 * (out["fp32"]["E"] - out["fp64"]["E"]),
+           "paired_diff_err_mK": 1e3 * float(diff.std(ddof=1) / math.sqrt(W)),
+           "combined_2sigma_mK": 2e3 * math.hypot(out["fp32"]["err"], out["fp64"]["err"])}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def _kernel_hash():
     import hashlib
     h = hashlib.sha1()
@@ -389,11 +550,19 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--equil", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--config", default="headline", choices=["headline", "uneven", "large", "fp64cmp"],
+                    help="headline: the benchmark line; the others measure the other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "uneven":
+        return run_uneven(args)
+    if args.config == "large":
+        return run_large(args)
+    if args.config == "fp64cmp":
+        return run_fp64cmp(args)
     return run_native(args)
 
 

@@ -411,9 +411,23 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
         // persistent mode: every resident CTA slot takes ready walkers in chunks of about a quarter
         // sweep of the largest walker, so that SMs stay evenly loaded when W is not a multiple of
         // the SM count
+        // resident CTAs per SM, cached so that calls under stream capture make no query
+        static std::mutex occ_mu;
+        static std::unordered_map<uint64_t, int> occ_cache;
+        int key_v[6] = {p.dev, o->precision, tpw, (int)v, G * tpw, (int)smem};
+        const uint64_t okey = fnv(key_v, sizeof key_v);
         int ctas = 0;
-        e = sweep_occupancy(o->precision, tpw, v, G * tpw, smem, &ctas);
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        {
+            std::lock_guard<std::mutex> lk(occ_mu);
+            auto it = occ_cache.find(okey);
+            if (it != occ_cache.end()) ctas = it->second;
+        }
+        if (ctas == 0) {
+            e = sweep_occupancy(o->precision, tpw, v, G * tpw, smem, &ctas);
+            if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+            std::lock_guard<std::mutex> lk(occ_mu);
+            occ_cache[okey] = ctas;
+        }
         const long long chunk = std::max(32, ((P.maxn + 3) / 4 + 31) / 32 * 32);
         long long total = 0;
         for (int w = 0; w < W; ++w) total += ((long long)nsweeps * d[w].n + chunk - 1) / chunk;

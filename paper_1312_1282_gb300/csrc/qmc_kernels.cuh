@@ -52,6 +52,46 @@ template <typename T> __device__ __forceinline__ T qnan();
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 
+// Running sum carried in two floats (Kahan compensation): keeps the ln psi and energy sums of the
+// FP32 path off the FP64 pipe (1/64 of the FP32 rate on this part) inside the hot loops; the
+// total goes to double once per chunk or pass.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// the ln psi carried along a chain: double in FP64 mode, compensated floats in FP32 mode
+template <typename T> struct LogPsiAcc {
+    double base;
+    KahanF inc;
+    __device__ __forceinline__ void add(T d)
+    {
+        if constexpr (std::is_same<T, float>::value)
+            inc.add(d);
+        else
+            base += d;
+    }
+    __device__ __forceinline__ double value() const
+    {
+        if constexpr (std::is_same<T, float>::value)
+            return base + inc.value();
+        else
+            return base;
+    }
+    __device__ __forceinline__ void set(double v)
+    {
+        base = v;
+        inc = KahanF();
+    }
+};
+
 struct SweepArgs {
     const DevWalker *walkers;  // [W] table
     const int *order;          // [W] processing order (longest walkers first)
@@ -331,7 +371,7 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
         Fz[i] = 0.f;
     }
     group_sync<TPW>(bar_id);
-    double sV = 0.0, sLap = 0.0;
+    KahanF kV, kLap;
     const int NBp = NB + (NB & 1);  // an even number of teams: a dummy block when NB is odd
     for (int r = 0; r < NBp - 1; ++r) {
         for (int k = warp; k < NBp / 2; k += NW) {
@@ -366,8 +406,8 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
             Fx[jb] += cx;
             Fy[jb] += cy;
             Fz[jb] += cz;
-            sV += (double)v;
-            sLap += 2.0 * (double)lap;
+            kV.add(v);
+            kLap.add(lap);
         }
         group_sync<TPW>(bar_id);
     }
@@ -402,14 +442,14 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
         Fx[i] += rx + cx;
         Fy[i] += ry + cy;
         Fz[i] += rz + cz;
-        sV += (double)v;
-        sLap += 2.0 * (double)lap;
+        kV.add(v);
+        kLap.add(lap);
     }
     group_sync<TPW>(bar_id);
     double sF2 = 0.0;
     for (int i = gtid; i < n; i += TPW) sF2 += (double)Fx[i] * Fx[i] + (double)Fy[i] * Fy[i] + (double)Fz[i] * Fz[i];
-    sV = group_sum<TPW>(sV, redD, phD, bar_id, gtid);
-    sLap = group_sum<TPW>(sLap, redD, phD, bar_id, gtid);
+    double sV = group_sum<TPW>(kV.value(), redD, phD, bar_id, gtid);
+    double sLap = 2.0 * group_sum<TPW>(kLap.value(), redD, phD, bar_id, gtid);  // each pair's term belongs to both atoms
     sF2 = group_sum<TPW>(sF2, redD, phD, bar_id, gtid);
     const double k = 0.5 * h2m;
     out[0] = sV;
@@ -658,7 +698,7 @@ template <int TPW, int K, typename T> __device__ __forceinline__ void group_sum_
 template <typename T, int MEXP, bool SYM, int TPW, int K, int KM>
 __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T *sy, T *sz, int nv,
                                            const int (&s)[K], const T (&dx)[K], const T (&dy)[K], const T (&dz)[K],
-                                           const T (&xi)[K], Recent<T, KM> &rec, double &lp, int &nacc, T *red,
+                                           const T (&xi)[K], Recent<T, KM> &rec, LogPsiAcc<T> &lp, int &nacc, T *red,
                                            T *dsm_base, int &ph, int bar_id, int gtid)
 {
     constexpr int VN = Vec<T>::N;
@@ -693,7 +733,7 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
         else
             acc[i] = exp(2.0 * delta) > xi[i];
         if (acc[i]) {
-            if (gtid == 0) lp += (double)delta;
+            if (gtid == 0) lp.add(delta);
             ++nacc;
         }
     }
@@ -742,7 +782,8 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, const GroupMem
     Jas<T, MEXP, SYM> J;
     J.init(d);
 
-    double lp = a.logpsi[slot];
+    LogPsiAcc<T> lp;
+    lp.set(a.logpsi[slot]);
     const unsigned long long k0 = a.sweep[slot];
     double *A = a.accum + 8 * (size_t)slot;
     int nacc = 0;
@@ -838,7 +879,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, const GroupMem
         group_sync<TPW>(bar_id);
         rec.clear();
         if (a.recompute_every > 0 && (kk + 1) % (unsigned long long)a.recompute_every == 0)
-            lp = group_log_psi<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, redD, phD, bar_id, gtid);
+            lp.set(group_log_psi<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, redD, phD, bar_id, gtid));
         if (a.energy_every > 0 && (kk + 1) % (unsigned long long)a.energy_every == 0) {
             double e[5];
             if constexpr (std::is_same<T, float>::value) {
@@ -866,7 +907,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, const GroupMem
     store_walker<T, TPW>(gx, n, pad, sx, sy, sz, gtid);
     if (gtid == 0) {
         A[7] += (double)nacc;  // integer-valued: exact in any order
-        a.logpsi[slot] = lp;
+        a.logpsi[slot] = lp.value();
         if (last) a.sweep[slot] = k0 + (unsigned long long)a.nsweeps;
     }
     return true;
