@@ -13,7 +13,9 @@
  *               (QMC_FP64).  Walker w occupies pos[d[w].offset ...] as three blocks of d[w].pad_n
  *               elements: x[pad_n] | y[pad_n] | z[pad_n] (structure of arrays).  Entries
  *               n .. pad_n-1 of each block are ignored on input and left unchanged.  Coordinates
- *               lie in [0, L]; the sweep keeps them there.
+ *               lie in [0, L]; the sweep keeps them there.  A walker stays in one CTA's shared
+ *               memory for a whole call when it fits (qmc_capacity); larger walkers are used in
+ *               place in HBM (their coordinates change during the call; slower, any size).
  *  Outputs:     DEVICE buffers owned by the caller, double precision, W-major.
  *  Streams:     `stream` is a cudaStream_t (NULL = legacy default stream).  Every compute call
  *               only enqueues work on it and returns; results are ready when the stream is.
@@ -41,7 +43,7 @@ extern "C" {
 #define QMC_OK 0
 #define QMC_ERR_ARG (-1)      /* null pointer, W <= 0, n < 2, bad padding/alignment, non-finite or
                                  out-of-range parameter */
-#define QMC_ERR_CAPACITY (-2) /* a walker does not fit one CTA's shared memory at this precision */
+#define QMC_ERR_CAPACITY (-2) /* qmc_init_walkers: the start lattice of a walker is too large */
 #define QMC_ERR_CUDA (-3)     /* a CUDA runtime call failed (message has the CUDA error string) */
 #define QMC_ERR_DEVICE (-4)   /* a kernel flagged a non-finite coordinate or ratio (qmc_status) */
 #define QMC_ERR_TIMEOUT (-5)  /* qmc_status: the stream did not finish within the time limit */
@@ -193,7 +195,7 @@ int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_options *opt, vo
                      uint64_t *sweep, uint64_t seed, int nsweeps, int energy_every, double *accum,
                      uint32_t *err, void *stream);
 
-/* Largest n one walker may have at this precision (shared-memory capacity of one CTA). */
+/* Largest n kept in one CTA's shared memory at this precision; larger walkers run from HBM. */
 int qmc_capacity(int precision);
 
 /*

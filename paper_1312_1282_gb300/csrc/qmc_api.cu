@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <list>
 #include <mutex>
@@ -136,6 +137,17 @@ size_t smem_group(int precision, int maxpad, int tpw, bool tile = false)
 {
     const int stride = stride_of(maxpad);
     return precision == QMC_FP64 ? group_smem<double>(stride, tpw, false) : group_smem<float>(stride, tpw, tile);
+}
+
+// Walkers whose coordinates do not fit one CTA's shared memory are used in place in HBM.
+// QMC_GLOBAL_WALKERS=1 in the environment forces that path for every batch (used by the tests).
+bool use_gmem(int precision, int maxpad, int tpw)
+{
+    static const bool forced = [] {
+        const char *e = std::getenv("QMC_GLOBAL_WALKERS");
+        return e && e[0] == '1';
+    }();
+    return forced || smem_group(precision, maxpad, tpw, false) > MAX_SMEM;
 }
 
 // the tiled local-energy pass (FP32) is used whenever its drift arrays fit next to G walkers
@@ -303,6 +315,7 @@ int choose_tpw(const Plan &P, const qmc_options *o, int dev, int nsm)
 // limit would cap residency.
 int choose_groups(const Plan &P, int precision, int tpw, int nsm)
 {
+    if (use_gmem(precision, P.maxpad, tpw)) return 1;
     int G = 1;
     if (tpw <= 128 && P.W > 24 * nsm) G = std::min(256 / tpw, (P.W + 24 * nsm - 1) / (24 * nsm));
     const bool tile = use_tile(precision, P.maxpad, tpw, 1);
@@ -310,12 +323,19 @@ int choose_groups(const Plan &P, int precision, int tpw, int nsm)
     return std::max(1, std::min(G, 8));
 }
 
-int check_capacity(const Plan &P, int precision, int tpw)
+// shared memory a launch needs per group and the layout flags that go with it
+struct Shape {
+    int stride, tile, gmem;
+    size_t smem;  // per group
+};
+Shape shape_of(const Plan &P, int precision, int tpw, int G, bool energy_pass)
 {
-    if (smem_group(precision, P.maxpad, tpw) > MAX_SMEM)
-        return fail(QMC_ERR_CAPACITY, "a walker with pad_n = %d does not fit shared memory at %s (max n %d)",
-                    P.maxpad, precision == QMC_FP64 ? "FP64" : "FP32", qmc_capacity(precision));
-    return QMC_OK;
+    Shape sh;
+    sh.gmem = use_gmem(precision, P.maxpad, tpw) ? 1 : 0;
+    sh.stride = sh.gmem ? 0 : stride_of(P.maxpad);
+    sh.tile = (!sh.gmem && energy_pass && use_tile(precision, P.maxpad, tpw, G)) ? 1 : 0;
+    sh.smem = sh.gmem ? smem_group(precision, 0, tpw, false) : smem_group(precision, P.maxpad, tpw, sh.tile != 0);
+    return sh;
 }
 
 int check_ptr(const void *p, const char *name, size_t align)
@@ -375,16 +395,17 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     if ((rc = prepare(d, W, o, st, p))) return rc;
     const Plan &P = *p.plan;
     const int tpw = tpw_force ? tpw_force : choose_tpw(P, o, p.dev, p.ds->nsm);
-    if ((rc = check_capacity(P, o->precision, tpw))) return rc;
     if (nsweeps == 0) return QMC_OK;
     const int G = choose_groups(P, o->precision, tpw, p.ds->nsm);
+    const Shape sh = shape_of(P, o->precision, tpw, G, true);
     SweepArgs a;
     a.walkers = P.d_walkers;
     a.order = P.d_order;
     a.W = W;
     a.G = G;
-    a.stride = stride_of(P.maxpad);
-    a.tile = use_tile(o->precision, P.maxpad, tpw, G) ? 1 : 0;
+    a.stride = sh.stride;
+    a.tile = sh.tile;
+    a.gmem = sh.gmem;
     a.pos = pos;
     a.logpsi = logpsi;
     a.sweep = reinterpret_cast<unsigned long long *>(sweep);
@@ -404,7 +425,7 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     a.q_slots = nullptr;
     a.q_prog = nullptr;
     int grid = (W + G - 1) / G;
-    const size_t smem = (size_t)G * smem_group(o->precision, P.maxpad, tpw, a.tile != 0);
+    const size_t smem = (size_t)G * sh.smem;
     const Variant v = variant_of(P, o);
     cudaError_t e;
     if (W > p.ds->nsm) {
@@ -460,12 +481,13 @@ int pass_impl(const qmc_walker_desc *d, int W, const qmc_options *o, const void 
     if ((rc = prepare(d, W, o, st, p))) return rc;
     const Plan &P = *p.plan;
     const int tpw = kind == 2 ? TRIAL_TPW : PASS_TPW;
-    if ((rc = check_capacity(P, o->precision, tpw))) return rc;
+    const Shape sh = shape_of(P, o->precision, tpw, 1, kind == 0);
     PassArgs a;
     a.walkers = P.d_walkers;
     a.W = W;
-    a.stride = stride_of(P.maxpad);
-    a.tile = (kind == 0 && use_tile(o->precision, P.maxpad, tpw, 1)) ? 1 : 0;
+    a.stride = sh.stride;
+    a.tile = sh.tile;
+    a.gmem = sh.gmem;
     a.pos = pos;
     a.out = out;
     a.h2m = o->hbar2_over_m;
@@ -473,7 +495,7 @@ int pass_impl(const qmc_walker_desc *d, int W, const qmc_options *o, const void 
     a.delta = delta;
     a.M = M;
     a.err = p.ds->err;
-    const size_t smem = smem_group(o->precision, P.maxpad, tpw, a.tile != 0);
+    const size_t smem = sh.smem;
     cudaError_t e = launch_pass(o->precision, variant_of(P, o), kind, W, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "pass launch");
     g_launches.fetch_add(1);
@@ -562,7 +584,7 @@ int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const 
     const int chunk_cap = pow2_at_least((P.maxn + 3) / 4);
     for (int tpw = 32; e == cudaSuccess && tpw <= 1024; tpw <<= 1) {
         if (tpw > chunk_cap) break;
-        if (smem_group(opt->precision, P.maxpad, tpw) > MAX_SMEM) continue;
+
         e = cudaMemcpyAsync(scratch, pos, bytes, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) break;
         rc = sweep_impl(d, W, opt, scratch, lp, sw, 0x7E57ull, 1, 0, acc, st, tpw);  // warm-up
@@ -768,7 +790,6 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
         return d[a].n != d[b].n ? d[a].n > d[b].n : a < b;
     });
     const int tpw = choose_tpw(P, opt, dev, nsm);
-    if ((rc = check_capacity(P, opt->precision, tpw))) return rc;
     if (nsweeps == 0) return QMC_OK;
 
     DevWalker *d_walkers = reinterpret_cast<DevWalker *>(base);
@@ -781,13 +802,15 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     if (e != cudaSuccess) return cuda_fail(e, "static walker table upload");
 
     const int G = choose_groups(P, opt->precision, tpw, nsm);
+    const Shape sh = shape_of(P, opt->precision, tpw, G, true);
     SweepArgs a;
     a.walkers = d_walkers;
     a.order = d_order;
     a.W = W;
     a.G = G;
-    a.stride = stride_of(P.maxpad);
-    a.tile = use_tile(opt->precision, P.maxpad, tpw, G) ? 1 : 0;
+    a.stride = sh.stride;
+    a.tile = sh.tile;
+    a.gmem = sh.gmem;
     a.pos = pos;
     a.logpsi = logpsi;
     a.sweep = reinterpret_cast<unsigned long long *>(sweep);
@@ -807,7 +830,7 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     a.q_slots = nullptr;
     a.q_prog = nullptr;
     const int grid = (W + G - 1) / G;
-    const size_t smem = (size_t)G * smem_group(opt->precision, P.maxpad, tpw, a.tile != 0);
+    const size_t smem = (size_t)G * sh.smem;
     e = launch_sweep(opt->precision, tpw, variant_of(P, opt), grid, G * tpw, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
     g_launches.fetch_add(1);

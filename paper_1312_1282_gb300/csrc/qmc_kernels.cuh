@@ -99,6 +99,7 @@ struct SweepArgs {
     int G;                     // walkers per CTA
     int stride;                // shared-memory block stride (elements): largest pad, rounded up to 32
     int tile;                  // 1: local energy by the tiled pass (needs the drift arrays in smem)
+    int gmem;                  // 1: walkers too large for shared memory stay in HBM (updated in place)
     void *pos;
     double *logpsi;
     unsigned long long *sweep;
@@ -169,7 +170,31 @@ template <typename T> struct GroupMem {
         fy = fx + stride;
         fz = fy + stride;
     }
+    // positions of a walker too large for shared memory: its own blocks in HBM, used in place
+    __device__ __forceinline__ void use_global(T *gx, int pad)
+    {
+        sx = gx;
+        sy = gx + pad;
+        sz = gx + 2 * (size_t)pad;
+    }
 };
+
+// Validation of a walker used in place (no copy): false in every thread of the group if a
+// coordinate is non-finite or outside [0, L].
+template <typename T, int TPW>
+__device__ bool check_walker(const T *gx, int n, int pad, T L, T *red, int &ph, int bar_id, int gtid)
+{
+    int bad = 0;
+    for (int j = gtid; j < n; j += TPW)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T a = gx[(size_t)k * pad + j];
+            bad |= !(a >= (T)0 && a <= L);
+        }
+    const T nbad = group_sum<TPW>((T)bad, red, ph, bar_id, gtid);
+    group_sync<TPW>(bar_id);
+    return nbad == (T)0;
+}
 
 // ----------------------------------------------------------------------------------------------
 // Load / store one walker
@@ -293,7 +318,8 @@ __device__ double group_log_psi(const Jas<T, MEXP, SYM> &J, const T *sx, const T
                         az = mi_abs(zi - Vec<T>::get(Z, e), L);
                 const T r2 = fma(ax, ax, fma(ay, ay, az * az));
                 const T uu = J.u(r2);
-                row += (r2 < hL2 && c * VN + e != i) ? uu : (T)0;
+                const int j = c * VN + e;
+                row += (r2 < hL2 && j != i && j < n) ? uu : (T)0;
             }
         }
         tot += (double)row;
@@ -492,7 +518,7 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
                 const T dy = mi_signed(yi - Vec<T>::get(Y, e), L, iL);
                 const T dz = mi_signed(zi - Vec<T>::get(Z, e), L, iL);
                 const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                const bool ok = (r2 < hL2) && (j != i);
+                const bool ok = (r2 < hL2) && (j != i) && (j < n);
                 const T q = Fn<T>::rsqrt(r2);
                 const T r = r2 * q;
                 const T f0 = J.fq(q, r);  // f(r) = c r^-m
@@ -503,10 +529,10 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
                     u1 += m * g0 * iw;
                     u2 += mm1 * g0 * (iw * iw);
                 }
-                const T g = ok ? u1 * q : (T)0;
-                fx = fma(g, dx, fx);
-                fy = fma(g, dy, fy);
-                fz = fma(g, dz, fz);
+                const T g = u1 * q;
+                fx += ok ? g * dx : (T)0;
+                fy += ok ? g * dy : (T)0;
+                fz += ok ? g * dz : (T)0;
                 if (upper) {
                     const bool half = ok && j > i;
                     lap += half ? fma((T)2 * u1, q, u2) : (T)0;
@@ -577,7 +603,7 @@ __device__ __forceinline__ T pair_du(const Jas<T, MEXP, SYM> &J, T xj, T yj, T z
 // other moves, u(|b_i - a_k|) - u(|a_i - a_k|), and the cross terms.
 template <typename T, int MEXP, bool SYM, int TPW, int K>
 __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const T *sx, const T *sy, const T *sz,
-                                               int nv, const int (&s)[K], const T (&ax)[K], const T (&ay)[K],
+                                               int n, int nv, const int (&s)[K], const T (&ax)[K], const T (&ay)[K],
                                                const T (&az)[K], const T (&bx)[K], const T (&by)[K],
                                                const T (&bz)[K], T (&S)[K], T *dsm, int gtid)
 {
@@ -616,6 +642,14 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
                     Vec<float>::set(Y, e, qnan<float>());
                     Vec<float>::set(Z, e, qnan<float>());
                 }
+            if (c == nv - 1)  // entries past n (HBM padding of a walker used in place)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * c + e >= n) {
+                        Vec<float>::set(X, e, qnan<float>());
+                        Vec<float>::set(Y, e, qnan<float>());
+                        Vec<float>::set(Z, e, qnan<float>());
+                    }
             const float2 xa = make_float2(X.x, X.y), xb = make_float2(X.z, X.w);
             const float2 ya = make_float2(Y.x, Y.y), yb = make_float2(Y.z, Y.w);
             const float2 za = make_float2(Z.x, Z.y), zb = make_float2(Z.z, Z.w);
@@ -645,6 +679,14 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
                     Vec<T>::set(Y, e, qnan<T>());
                     Vec<T>::set(Z, e, qnan<T>());
                 }
+            if (c == nv - 1)  // entries past n (HBM padding of a walker used in place)
+#pragma unroll
+                for (int e = 0; e < VN; ++e)
+                    if (VN * c + e >= n) {
+                        Vec<T>::set(X, e, qnan<T>());
+                        Vec<T>::set(Y, e, qnan<T>());
+                        Vec<T>::set(Z, e, qnan<T>());
+                    }
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
                 const T xj = Vec<T>::get(X, e), yj = Vec<T>::get(Y, e), zj = Vec<T>::get(Z, e);
@@ -696,7 +738,7 @@ template <int TPW, int K, typename T> __device__ __forceinline__ void group_sum_
 
 // One batch of K moves.  Returns false on a non-finite ratio (identically in every thread).
 template <typename T, int MEXP, bool SYM, int TPW, int K, int KM>
-__device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T *sy, T *sz, int nv,
+__device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T *sy, T *sz, int n, int nv,
                                            const int (&s)[K], const T (&dx)[K], const T (&dy)[K], const T (&dz)[K],
                                            const T (&xi)[K], Recent<T, KM> &rec, LogPsiAcc<T> &lp, int &nacc, T *red,
                                            T *dsm_base, int &ph, int bar_id, int gtid)
@@ -715,7 +757,7 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
         bz[i] = wrap(az[i] + dz[i], L);
     }
     T *dsm = dsm_base + ph * KM * KM;
-    batch_partners<T, MEXP, SYM, TPW, K>(J, sx, sy, sz, nv, s, ax, ay, az, bx, by, bz, S, dsm, gtid);
+    batch_partners<T, MEXP, SYM, TPW, K>(J, sx, sy, sz, n, nv, s, ax, ay, az, bx, by, bz, S, dsm, gtid);
     group_sum_k<TPW, K>(S, red, ph, bar_id, gtid);
     ph ^= 1;
     bool acc[K];
@@ -763,9 +805,11 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
 // Returns false if the walker faulted (nothing of it is written back).
 // ----------------------------------------------------------------------------------------------
 template <typename T, int MEXP, bool SYM, int TPW>
-__device__ bool run_range(const SweepArgs &a, const DevWalker &d, const GroupMem<T> &mem, int gtid, int bar_id,
+__device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> mem, int gtid, int bar_id,
                           long long m_begin, long long m_end, bool last)
 {
+    T *const gx = reinterpret_cast<T *>(a.pos) + d.off;
+    if (a.gmem) mem.use_global(gx, d.pad);
     T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
     double *redD = mem.redD;
     constexpr int VN = Vec<T>::N;
@@ -773,9 +817,9 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, const GroupMem
     const int slot = d.slot;
     const T L = (T)d.L, step = (T)d.step;
     int phT = 0, phD = 0;
-    T *gx = reinterpret_cast<T *>(a.pos) + d.off;
-
-    if (!load_walker<T, TPW>(gx, n, pad, a.stride, L, sx, sy, sz, redT, phT, bar_id, gtid)) {
+    const bool loaded = a.gmem ? check_walker<T, TPW>(gx, n, pad, L, redT, phT, bar_id, gtid)
+                               : load_walker<T, TPW>(gx, n, pad, a.stride, L, sx, sy, sz, redT, phT, bar_id, gtid);
+    if (!loaded) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
         return false;
     }
@@ -849,13 +893,13 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, const GroupMem
                     for (int q = i + 1; q < KB; ++q) distinct &= bs[i] != bs[q];
                 bool ok = true;
                 if (distinct) {
-                    ok = move_batch<T, MEXP, SYM, TPW, KB, KB>(J, sx, sy, sz, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
+                    ok = move_batch<T, MEXP, SYM, TPW, KB, KB>(J, sx, sy, sz, n, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
                                                                nacc, redT, dsm, phT, bar_id, gtid);
                 } else {
                     for (int i = 0; i < KB && ok; ++i) {
                         const int s1[1] = {bs[i]};
                         const T x1[1] = {bdx[i]}, y1[1] = {bdy[i]}, z1[1] = {bdz[i]}, c1[1] = {bxi[i]};
-                        ok = move_batch<T, MEXP, SYM, TPW, 1, KB>(J, sx, sy, sz, nv, s1, x1, y1, z1, c1, rec, lp,
+                        ok = move_batch<T, MEXP, SYM, TPW, 1, KB>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp,
                                                                   nacc, redT, dsm, phT, bar_id, gtid);
                     }
                 }
@@ -868,7 +912,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, const GroupMem
                 const int s1[1] = {__shfl_sync(FULL, my_s, tt)};
                 const T x1[1] = {__shfl_sync(FULL, mdx, tt)}, y1[1] = {__shfl_sync(FULL, mdy, tt)},
                         z1[1] = {__shfl_sync(FULL, mdz, tt)}, c1[1] = {__shfl_sync(FULL, mxi, tt)};
-                if (!move_batch<T, MEXP, SYM, TPW, 1, KB>(J, sx, sy, sz, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
+                if (!move_batch<T, MEXP, SYM, TPW, 1, KB>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
                                                           dsm, phT, bar_id, gtid)) {
                     if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
                     return false;
@@ -904,7 +948,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, const GroupMem
         }
     }
     group_sync<TPW>(bar_id);
-    store_walker<T, TPW>(gx, n, pad, sx, sy, sz, gtid);
+    if (!a.gmem) store_walker<T, TPW>(gx, n, pad, sx, sy, sz, gtid);
     if (gtid == 0) {
         A[7] += (double)nacc;  // integer-valued: exact in any order
         a.logpsi[slot] = lp.value();
@@ -967,9 +1011,10 @@ __device__ __forceinline__ void queue_push(const SweepArgs &a, int w)
 
 // CTAs hold up to 256 threads (TPW <= 256) or exactly one group; at least 1024 resident threads
 // per SM, i.e. at most 64 registers per thread.
-// TPW = 128 (one 4-warp group per walker, a few walkers per SM) gets up to 128 registers.
+// Groups of up to 128 threads get up to 128 registers (at least 512 resident threads per SM);
+// larger groups keep 64 registers so that 1024 threads fit.
 template <int TPW> constexpr int cta_bound() { return TPW > 256 ? TPW : 256; }
-template <int TPW> constexpr int min_blocks() { return TPW == 128 ? 2 : 1024 / cta_bound<TPW>(); }
+template <int TPW> constexpr int min_blocks() { return TPW <= 128 ? 2 : 1024 / cta_bound<TPW>(); }
 
 template <typename T, int MEXP, bool SYM, int TPW>
 __global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_kernel(SweepArgs a)
@@ -1020,6 +1065,7 @@ struct PassArgs {
     int W;
     int stride;
     int tile;
+    int gmem;
     const void *pos;
     double *out;
     double h2m;
@@ -1044,7 +1090,14 @@ __global__ void __launch_bounds__(TPW) pass_kernel(PassArgs a, int kind)
     int phT = 0, phD = 0;
     constexpr int VN = Vec<T>::N;
     const T *gx = reinterpret_cast<const T *>(a.pos) + d.off;
-    if (!load_walker<T, TPW>(gx, d.n, d.pad, a.stride, (T)d.L, sx, sy, sz, redT, phT, 1, gtid)) {
+    if (a.gmem) {
+        mem.use_global(const_cast<T *>(gx), d.pad);
+        sx = mem.sx;
+        sy = mem.sy;
+        sz = mem.sz;
+    }
+    if (!(a.gmem ? check_walker<T, TPW>(gx, d.n, d.pad, (T)d.L, redT, phT, 1, gtid)
+                 : load_walker<T, TPW>(gx, d.n, d.pad, a.stride, (T)d.L, sx, sy, sz, redT, phT, 1, gtid))) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
         return;
     }
@@ -1085,7 +1138,14 @@ __global__ void __launch_bounds__(TPW) trial_kernel(PassArgs a)
     constexpr int VN = Vec<T>::N;
     const T *gx = reinterpret_cast<const T *>(a.pos) + d.off;
     const T L = (T)d.L;
-    if (!load_walker<T, TPW>(gx, d.n, d.pad, a.stride, L, sx, sy, sz, redT, phT, 1, gtid)) {
+    if (a.gmem) {
+        mem.use_global(const_cast<T *>(gx), d.pad);
+        sx = mem.sx;
+        sy = mem.sy;
+        sz = mem.sz;
+    }
+    if (!(a.gmem ? check_walker<T, TPW>(gx, d.n, d.pad, L, redT, phT, 1, gtid)
+                 : load_walker<T, TPW>(gx, d.n, d.pad, a.stride, L, sx, sy, sz, redT, phT, 1, gtid))) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
         return;
     }
@@ -1107,7 +1167,7 @@ __global__ void __launch_bounds__(TPW) trial_kernel(PassArgs a)
         const T bx[1] = {wrap(ax[0] + (T)a.delta[3 * mi], L)}, by[1] = {wrap(ay[0] + (T)a.delta[3 * mi + 1], L)},
                 bz[1] = {wrap(az[0] + (T)a.delta[3 * mi + 2], L)};
         T S[1];
-        batch_partners<T, MEXP, SYM, TPW, 1>(J, sx, sy, sz, nv, s1, ax, ay, az, bx, by, bz, S, nullptr, gtid);
+        batch_partners<T, MEXP, SYM, TPW, 1>(J, sx, sy, sz, d.n, nv, s1, ax, ay, az, bx, by, bz, S, nullptr, gtid);
         const T delta = group_sum<TPW>(S[0], redT, phT, 1, gtid);
         if (gtid == 0) a.out[mi] = (double)delta;
     }
@@ -1133,7 +1193,14 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
     using V = typename Vec<T>::type;
     const T *gx = reinterpret_cast<const T *>(a.pos) + d.off;
     const T L = (T)d.L, iL = (T)1 / L, hL2 = (T)(0.25 * d.L * d.L);
-    if (!load_walker<T, TPW>(gx, d.n, d.pad, a.stride, L, sx, sy, sz, redT, phT, 1, gtid)) {
+    if (a.gmem) {
+        mem.use_global(const_cast<T *>(gx), d.pad);
+        sx = mem.sx;
+        sy = mem.sy;
+        sz = mem.sz;
+    }
+    if (!(a.gmem ? check_walker<T, TPW>(gx, d.n, d.pad, L, redT, phT, 1, gtid)
+                 : load_walker<T, TPW>(gx, d.n, d.pad, a.stride, L, sx, sy, sz, redT, phT, 1, gtid))) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
         return;
     }
@@ -1157,7 +1224,7 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
                 const T dy = mi_signed(yi - Vec<T>::get(Y, e), L, iL);
                 const T dz = mi_signed(zi - Vec<T>::get(Z, e), L, iL);
                 const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                const bool ok = (r2 < hL2) && (cc * VN + e != i);
+                const bool ok = (r2 < hL2) && (cc * VN + e != i) && (cc * VN + e < n);
                 const T q = Fn<T>::rsqrt(r2);
                 const T r = r2 * q;
                 const T lbr = lnb + Fn<T>::log(q);  // ln(b/r)

@@ -128,13 +128,10 @@ def test_padding_is_ignored_and_left_alone():
 
 def test_capacity_and_argument_errors():
     big = lattice_batch([2], q.QMC_FP32)
-    over = q.qmc_capacity(q.QMC_FP32) + 1000
-    rows = [(over, over, 0, 0, 100.0, 0, 3.07, 5.0, 0.8)]
+    # start lattices beyond one CTA's shared memory are refused on the host, before any launch
+    rows = [(60000, 60000, 0, 0, 140.0, 0, 3.07, 5.0, 0.8)]
     with pytest.raises(q.QmcError, match="CAPACITY"):
-        q.qmc_local_energy(q.descs(rows), q.options(), big.pos, zeros(5))
-    rows = [(10000, 10000, 0, 0, 77.0, 0, 3.07, 5.0, 0.8)]
-    with pytest.raises(q.QmcError, match="CAPACITY"):
-        q.qmc_local_energy(q.descs(rows), q.options(precision=q.QMC_FP64), big.pos, zeros(5))
+        q.qmc_init_walkers(q.descs(rows), 1, 0.1, q.options(), big.pos)
     for bad in [(1, 4, 0, 0, 10.0, 0, 3.0, 5.0, 0.8), (8, 6, 0, 0, 10.0, 0, 3.0, 5.0, 0.8),
                 (8, 8, 2, 0, 10.0, 0, 3.0, 5.0, 0.8), (8, 8, 0, 0, 0.0, 0.0, 3.0, 5.0, 0.8),
                 (8, 8, 0, 0, 10.0, 0, -1.0, 5.0, 0.8), (8, 8, 0, 0, 10.0, 0, 3.0, 5.0, 11.0),
