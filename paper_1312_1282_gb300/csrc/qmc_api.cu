@@ -26,6 +26,9 @@ using namespace qmc;
 namespace {
 
 constexpr size_t MAX_SMEM = 232448;  // opt-in dynamic shared memory per CTA (227 KB)
+#ifndef QMC_CHUNK_DIV
+#define QMC_CHUNK_DIV 8  // persistent sweep: chunks of 1/QMC_CHUNK_DIV sweep of the largest walker
+#endif
 constexpr int MAX_DEVICES = 64;
 constexpr size_t MAX_PLANS = 32;
 
@@ -429,9 +432,9 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     const Variant v = variant_of(P, o);
     cudaError_t e;
     if (W > p.ds->nsm) {
-        // persistent mode: every resident CTA slot takes ready walkers in chunks of about a quarter
-        // sweep of the largest walker, so that SMs stay evenly loaded when W is not a multiple of
-        // the SM count
+        // persistent mode: every resident CTA slot takes ready walkers in chunks of about an eighth
+        // of a sweep of the largest walker, so that SMs stay evenly loaded when W is not a multiple
+        // of the SM count
         // resident CTAs per SM, cached so that calls under stream capture make no query
         static std::mutex occ_mu;
         static std::unordered_map<uint64_t, int> occ_cache;
@@ -449,7 +452,7 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
             std::lock_guard<std::mutex> lk(occ_mu);
             occ_cache[okey] = ctas;
         }
-        const long long chunk = std::max(32, ((P.maxn + 3) / 4 + 31) / 32 * 32);
+        const long long chunk = std::max(32, ((P.maxn + QMC_CHUNK_DIV - 1) / QMC_CHUNK_DIV + 31) / 32 * 32);
         long long total = 0;
         for (int w = 0; w < W; ++w) total += ((long long)nsweeps * d[w].n + chunk - 1) / chunk;
         if (ctas > 0 && total < (1ll << 31)) {

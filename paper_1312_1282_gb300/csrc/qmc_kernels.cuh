@@ -382,6 +382,95 @@ template <int MEXP, bool SYM> struct TilePair {
     }
 };
 
+// Two tile steps at once (partners j0 and j1 of the same row atom), packed f32x2 arithmetic for
+// exponent 5 and the symmetrised u; the general case evaluates the scalar form twice.
+template <int MEXP, bool SYM> struct TilePair2 {
+    TilePair<MEXP, SYM> P;
+    float2 L2, iL2, nL2, M2, nM2, m1, c2, nm2, m2, mm12, two2, irm2, rm2sq, C6, C8, C10, beta2, nalpha2, l2e2, A2, eps2;
+    __device__ __forceinline__ TilePair2(const Jas<float, MEXP, SYM> &j) : P(j)
+    {
+        const float rm = 2.963f;
+        L2 = make_float2(j.L, j.L);
+        iL2 = make_float2(1.f / j.L, 1.f / j.L);
+        nL2 = make_float2(-j.L, -j.L);
+        M2 = make_float2(12582912.f, 12582912.f);
+        nM2 = make_float2(-12582912.f, -12582912.f);
+        m1 = make_float2(-1.f, -1.f);
+        c2 = make_float2(j.c, j.c);
+        nm2 = make_float2(-j.m, -j.m);
+        m2 = make_float2(j.m, j.m);
+        mm12 = make_float2(j.m * (j.m + 1.f), j.m * (j.m + 1.f));
+        two2 = make_float2(2.f, 2.f);
+        irm2 = make_float2(1.f / rm, 1.f / rm);
+        rm2sq = make_float2(rm * rm, rm * rm);
+        C6 = make_float2(1.36745214f, 1.36745214f);
+        C8 = make_float2(0.42123807f, 0.42123807f);
+        C10 = make_float2(0.17473318f, 0.17473318f);
+        beta2 = make_float2(-2.27965105f, -2.27965105f);
+        nalpha2 = make_float2(-10.43329537f, -10.43329537f);
+        l2e2 = make_float2(1.4426950408889634f, 1.4426950408889634f);
+        A2 = make_float2(1.8443101e5f, 1.8443101e5f);
+        eps2 = make_float2(10.948f, 10.948f);
+    }
+    __device__ __forceinline__ float2 mi(float2 d) const
+    {
+        const float2 t = __fadd2_rn(__ffma2_rn(d, iL2, M2), nM2);  // round(d / L)
+        return __ffma2_rn(nL2, t, d);
+    }
+    __device__ __forceinline__ void operator()(float xi, float yi, float zi, float2 xj, float2 yj, float2 zj,
+                                               bool take0, bool take1, float2 &gx, float2 &gy, float2 &gz,
+                                               float2 &lap, float2 &v) const
+    {
+        if constexpr (MEXP == 5 && SYM) {
+            const float2 dx = mi(__ffma2_rn(xj, m1, make_float2(xi, xi)));
+            const float2 dy = mi(__ffma2_rn(yj, m1, make_float2(yi, yi)));
+            const float2 dz = mi(__ffma2_rn(zj, m1, make_float2(zi, zi)));
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const bool ok0 = take0 && r2.x < P.hL2, ok1 = take1 && r2.y < P.hL2;
+            const float2 q = make_float2(rsqrt_a(r2.x), rsqrt_a(r2.y));
+            const float2 r = __fmul2_rn(r2, q);
+            const float2 q2 = __fmul2_rn(q, q);
+            const float2 f0 = __fmul2_rn(c2, __fmul2_rn(__fmul2_rn(q2, q2), q));
+            float2 u1 = __fmul2_rn(__fmul2_rn(nm2, f0), q);
+            float2 u2 = __fmul2_rn(__fmul2_rn(mm12, f0), q2);
+            const float2 w = __ffma2_rn(r, m1, L2);
+            const float2 iw = make_float2(rcp_a(w.x), rcp_a(w.y));
+            const float2 w2 = __fmul2_rn(iw, iw);
+            const float2 g0 = __fmul2_rn(c2, __fmul2_rn(__fmul2_rn(w2, w2), iw));
+            u1 = __ffma2_rn(__fmul2_rn(m2, g0), iw, u1);
+            u2 = __ffma2_rn(__fmul2_rn(mm12, g0), w2, u2);
+            float2 g = __fmul2_rn(u1, q);
+            g = make_float2(ok0 ? g.x : 0.f, ok1 ? g.y : 0.f);
+            gx = __fmul2_rn(g, dx);
+            gy = __fmul2_rn(g, dy);
+            gz = __fmul2_rn(g, dz);
+            const float2 lp = __ffma2_rn(__fmul2_rn(two2, u1), q, u2);
+            lap = make_float2(ok0 ? lp.x : 0.f, ok1 ? lp.y : 0.f);
+            // Aziz II; the damping factor only where some lane has x < D
+            const float2 x = __fmul2_rn(r, irm2);
+            const float2 y = __fmul2_rn(q2, rm2sq);
+            const float2 disp = __fmul2_rn(__fmul2_rn(__fmul2_rn(y, y), y), __ffma2_rn(__ffma2_rn(C10, y, C8), y, C6));
+            const float2 ea = __fmul2_rn(__fmul2_rn(x, __ffma2_rn(beta2, x, nalpha2)), l2e2);
+            const float2 rep = __fmul2_rn(A2, make_float2(ex2_a(ea.x), ex2_a(ea.y)));
+            float2 F = make_float2(1.f, 1.f);
+            const float D = 1.4826f;
+            const bool d0 = ok0 && x.x < D, d1 = ok1 && x.y < D;
+            if (__any_sync(FULL, d0 || d1)) {
+                const float t0 = fmaf(D * 2.963f, q.x, -1.f), t1 = fmaf(D * 2.963f, q.y, -1.f);
+                F.x = d0 ? Fn<float>::exp(-(t0 * t0)) : 1.f;
+                F.y = d1 ? Fn<float>::exp(-(t1 * t1)) : 1.f;
+            }
+            const float2 vv = __fmul2_rn(eps2, __ffma2_rn(__fmul2_rn(F, m1), disp, rep));
+            v = make_float2(ok0 ? vv.x : 0.f, ok1 ? vv.y : 0.f);
+        } else {
+            P(xi, yi, zi, xj.x, yj.x, zj.x, take0, gx.x, gy.x, gz.x, lap.x, v.x);
+            P(xi, yi, zi, xj.y, yj.y, zj.y, take1, gx.y, gy.y, gz.y, lap.y, v.y);
+        }
+    }
+};
+
 template <int MEXP, bool SYM, int TPW>
 __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *sx, const float *sy, const float *sz,
                                    float *Fx, float *Fy, float *Fz, int n, double h2m, double *redD, int &phD,
@@ -390,7 +479,7 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
     constexpr int NW = TPW / 32;
     const int lane = gtid & 31, warp = gtid >> 5;
     const int NB = (n + 31) >> 5;
-    const TilePair<MEXP, SYM> P(J);
+    const TilePair2<MEXP, SYM> P2(J);
     for (int i = gtid; i < NB * 32; i += TPW) {
         Fx[i] = 0.f;
         Fy[i] = 0.f;
@@ -407,20 +496,21 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
             const int i = 32 * a + lane;
             const float xi = sx[i], yi = sy[i], zi = sz[i];
             float rx = 0.f, ry = 0.f, rz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, lap = 0.f, v = 0.f;
-#pragma unroll 2
-            for (int t = 0; t < 32; ++t) {
-                const int j = 32 * b + ((lane + t) & 31);
-                float gx, gy, gz, l1, v1;
-                P(xi, yi, zi, sx[j], sy[j], sz[j], true, gx, gy, gz, l1, v1);
-                rx += gx;
-                ry += gy;
-                rz += gz;
-                cx -= gx;
-                cy -= gy;
-                cz -= gz;
-                lap += l1;
-                v += v1;
-                const int src = (lane + 1) & 31;
+            const int src = (lane + 1) & 31;
+            for (int t = 0; t < 32; t += 2) {
+                const int j0 = 32 * b + ((lane + t) & 31), j1 = 32 * b + ((lane + t + 1) & 31);
+                float2 gx, gy, gz, l2, v2;
+                P2(xi, yi, zi, make_float2(sx[j0], sx[j1]), make_float2(sy[j0], sy[j1]), make_float2(sz[j0], sz[j1]),
+                   true, true, gx, gy, gz, l2, v2);
+                rx += gx.x + gx.y;
+                ry += gy.x + gy.y;
+                rz += gz.x + gz.y;
+                lap += l2.x + l2.y;
+                v += v2.x + v2.y;
+                // partner drift: step t belongs to the register now here, step t+1 to the next one
+                cx = __shfl_sync(FULL, cx - gx.x, src) - gx.y;
+                cy = __shfl_sync(FULL, cy - gy.x, src) - gy.y;
+                cz = __shfl_sync(FULL, cz - gz.x, src) - gz.y;
                 cx = __shfl_sync(FULL, cx, src);
                 cy = __shfl_sync(FULL, cy, src);
                 cz = __shfl_sync(FULL, cz, src);
@@ -441,23 +531,24 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
         const int i = 32 * b + lane;
         const float xi = sx[i], yi = sy[i], zi = sz[i];
         float rx = 0.f, ry = 0.f, rz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, lap = 0.f, v = 0.f;
-        for (int t = 1; t <= 16; ++t) {
-            const int j = 32 * b + ((lane + t) & 31);
-            float gx, gy, gz, l1, v1;
-            P(xi, yi, zi, sx[j], sy[j], sz[j], t < 16 || lane < 16, gx, gy, gz, l1, v1);
-            rx += gx;
-            ry += gy;
-            rz += gz;
-            cx -= gx;
-            cy -= gy;
-            cz -= gz;
-            lap += l1;
-            v += v1;
-            if (t < 16) {
-                const int src = (lane + 1) & 31;
-                cx = __shfl_sync(FULL, cx, src);
-                cy = __shfl_sync(FULL, cy, src);
-                cz = __shfl_sync(FULL, cz, src);
+        const int src1 = (lane + 1) & 31;
+        for (int t = 1; t <= 16; t += 2) {
+            const int j0 = 32 * b + ((lane + t) & 31), j1 = 32 * b + ((lane + t + 1) & 31);
+            float2 gx, gy, gz, l2, v2;
+            P2(xi, yi, zi, make_float2(sx[j0], sx[j1]), make_float2(sy[j0], sy[j1]), make_float2(sz[j0], sz[j1]),
+               true, t + 1 < 16 || lane < 16, gx, gy, gz, l2, v2);
+            rx += gx.x + gx.y;
+            ry += gy.x + gy.y;
+            rz += gz.x + gz.y;
+            lap += l2.x + l2.y;
+            v += v2.x + v2.y;
+            cx = __shfl_sync(FULL, cx - gx.x, src1) - gx.y;  // step t, then step t+1
+            cy = __shfl_sync(FULL, cy - gy.x, src1) - gy.y;
+            cz = __shfl_sync(FULL, cz - gz.x, src1) - gz.y;
+            if (t + 1 < 16) {
+                cx = __shfl_sync(FULL, cx, src1);
+                cy = __shfl_sync(FULL, cy, src1);
+                cz = __shfl_sync(FULL, cz, src1);
             }
         }
         // after step 16 lane l holds the partner total of atom 32b + ((l + 16) mod 32)
@@ -601,7 +692,7 @@ __device__ __forceinline__ T pair_du(const Jas<T, MEXP, SYM> &J, T xj, T yj, T z
 // atom is replaced by NaN, which contributes exactly zero to every sum (the clamp), so the loop
 // has a single fast path; afterwards the owner of atom s_k adds its terms as a partner of the
 // other moves, u(|b_i - a_k|) - u(|a_i - a_k|), and the cross terms.
-template <typename T, int MEXP, bool SYM, int TPW, int K>
+template <typename T, int MEXP, bool SYM, int TPW, int K, bool GM = false>
 __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const T *sx, const T *sy, const T *sz,
                                                int n, int nv, const int (&s)[K], const T (&ax)[K], const T (&ay)[K],
                                                const T (&az)[K], const T (&bx)[K], const T (&by)[K],
@@ -642,7 +733,7 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
                     Vec<float>::set(Y, e, qnan<float>());
                     Vec<float>::set(Z, e, qnan<float>());
                 }
-            if (c == nv - 1)  // entries past n (HBM padding of a walker used in place)
+            if (GM && c == nv - 1)  // entries past n (HBM padding of a walker used in place)
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                     if (4 * c + e >= n) {
@@ -679,7 +770,7 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
                     Vec<T>::set(Y, e, qnan<T>());
                     Vec<T>::set(Z, e, qnan<T>());
                 }
-            if (c == nv - 1)  // entries past n (HBM padding of a walker used in place)
+            if (GM && c == nv - 1)  // entries past n (HBM padding of a walker used in place)
 #pragma unroll
                 for (int e = 0; e < VN; ++e)
                     if (VN * c + e >= n) {
@@ -737,7 +828,7 @@ template <int TPW, int K, typename T> __device__ __forceinline__ void group_sum_
 }
 
 // One batch of K moves.  Returns false on a non-finite ratio (identically in every thread).
-template <typename T, int MEXP, bool SYM, int TPW, int K, int KM>
+template <typename T, int MEXP, bool SYM, int TPW, int K, int KM, bool GM>
 __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T *sy, T *sz, int n, int nv,
                                            const int (&s)[K], const T (&dx)[K], const T (&dy)[K], const T (&dz)[K],
                                            const T (&xi)[K], Recent<T, KM> &rec, LogPsiAcc<T> &lp, int &nacc, T *red,
@@ -757,7 +848,7 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
         bz[i] = wrap(az[i] + dz[i], L);
     }
     T *dsm = dsm_base + ph * KM * KM;
-    batch_partners<T, MEXP, SYM, TPW, K>(J, sx, sy, sz, n, nv, s, ax, ay, az, bx, by, bz, S, dsm, gtid);
+    batch_partners<T, MEXP, SYM, TPW, K, GM>(J, sx, sy, sz, n, nv, s, ax, ay, az, bx, by, bz, S, dsm, gtid);
     group_sum_k<TPW, K>(S, red, ph, bar_id, gtid);
     ph ^= 1;
     bool acc[K];
@@ -804,12 +895,14 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
 // end; `last` marks the range that ends the call (the walker's sweep counter advances then).
 // Returns false if the walker faulted (nothing of it is written back).
 // ----------------------------------------------------------------------------------------------
-template <typename T, int MEXP, bool SYM, int TPW>
+template <typename T, int MEXP, bool SYM, int TPW, bool GM>
 __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> mem, int gtid, int bar_id,
                           long long m_begin, long long m_end, bool last)
 {
+    // GM: the walker is used in place in HBM; otherwise it is copied to shared memory (the
+    // address space is a compile-time property so that shared loads stay shared loads)
     T *const gx = reinterpret_cast<T *>(a.pos) + d.off;
-    if (a.gmem) mem.use_global(gx, d.pad);
+    if constexpr (GM) mem.use_global(gx, d.pad);
     T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
     double *redD = mem.redD;
     constexpr int VN = Vec<T>::N;
@@ -817,8 +910,11 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
     const int slot = d.slot;
     const T L = (T)d.L, step = (T)d.step;
     int phT = 0, phD = 0;
-    const bool loaded = a.gmem ? check_walker<T, TPW>(gx, n, pad, L, redT, phT, bar_id, gtid)
-                               : load_walker<T, TPW>(gx, n, pad, a.stride, L, sx, sy, sz, redT, phT, bar_id, gtid);
+    bool loaded;
+    if constexpr (GM)
+        loaded = check_walker<T, TPW>(gx, n, pad, L, redT, phT, bar_id, gtid);
+    else
+        loaded = load_walker<T, TPW>(gx, n, pad, a.stride, L, sx, sy, sz, redT, phT, bar_id, gtid);
     if (!loaded) {
         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
         return false;
@@ -893,13 +989,13 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
                     for (int q = i + 1; q < KB; ++q) distinct &= bs[i] != bs[q];
                 bool ok = true;
                 if (distinct) {
-                    ok = move_batch<T, MEXP, SYM, TPW, KB, KB>(J, sx, sy, sz, n, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
+                    ok = move_batch<T, MEXP, SYM, TPW, KB, KB, GM>(J, sx, sy, sz, n, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
                                                                nacc, redT, dsm, phT, bar_id, gtid);
                 } else {
                     for (int i = 0; i < KB && ok; ++i) {
                         const int s1[1] = {bs[i]};
                         const T x1[1] = {bdx[i]}, y1[1] = {bdy[i]}, z1[1] = {bdz[i]}, c1[1] = {bxi[i]};
-                        ok = move_batch<T, MEXP, SYM, TPW, 1, KB>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp,
+                        ok = move_batch<T, MEXP, SYM, TPW, 1, KB, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp,
                                                                   nacc, redT, dsm, phT, bar_id, gtid);
                     }
                 }
@@ -912,7 +1008,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
                 const int s1[1] = {__shfl_sync(FULL, my_s, tt)};
                 const T x1[1] = {__shfl_sync(FULL, mdx, tt)}, y1[1] = {__shfl_sync(FULL, mdy, tt)},
                         z1[1] = {__shfl_sync(FULL, mdz, tt)}, c1[1] = {__shfl_sync(FULL, mxi, tt)};
-                if (!move_batch<T, MEXP, SYM, TPW, 1, KB>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
+                if (!move_batch<T, MEXP, SYM, TPW, 1, KB, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
                                                           dsm, phT, bar_id, gtid)) {
                     if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
                     return false;
@@ -926,7 +1022,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
             lp.set(group_log_psi<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, redD, phD, bar_id, gtid));
         if (a.energy_every > 0 && (kk + 1) % (unsigned long long)a.energy_every == 0) {
             double e[5];
-            if constexpr (std::is_same<T, float>::value) {
+            if constexpr (std::is_same<T, float>::value && !GM) {
                 if (a.tile)
                     group_energy_tiled<MEXP, SYM, TPW>(J, sx, sy, sz, mem.fx, mem.fy, mem.fz, n, a.h2m, redD, phD,
                                                        bar_id, gtid, e);
@@ -948,7 +1044,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
         }
     }
     group_sync<TPW>(bar_id);
-    if (!a.gmem) store_walker<T, TPW>(gx, n, pad, sx, sy, sz, gtid);
+    if constexpr (!GM) store_walker<T, TPW>(gx, n, pad, sx, sy, sz, gtid);
     if (gtid == 0) {
         A[7] += (double)nacc;  // integer-valued: exact in any order
         a.logpsi[slot] = lp.value();
@@ -1011,10 +1107,10 @@ __device__ __forceinline__ void queue_push(const SweepArgs &a, int w)
 
 // CTAs hold up to 256 threads (TPW <= 256) or exactly one group; at least 1024 resident threads
 // per SM, i.e. at most 64 registers per thread.
-// Groups of up to 128 threads get up to 128 registers (at least 512 resident threads per SM);
-// larger groups keep 64 registers so that 1024 threads fit.
+// Up to 128 registers per thread (at least 512 resident threads per SM) except for groups of
+// 1024 threads, which keep 64.
 template <int TPW> constexpr int cta_bound() { return TPW > 256 ? TPW : 256; }
-template <int TPW> constexpr int min_blocks() { return TPW <= 128 ? 2 : 1024 / cta_bound<TPW>(); }
+template <int TPW> constexpr int min_blocks() { return TPW <= 256 ? 2 : 1; }
 
 template <typename T, int MEXP, bool SYM, int TPW>
 __global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_kernel(SweepArgs a)
@@ -1027,7 +1123,11 @@ __global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_ker
     mem.bind(smem + (size_t)g * group_smem<T>(a.stride, TPW, a.tile), a.stride, TPW, a.tile);
     if (!a.dynamic) {
         const DevWalker d = a.walkers[a.order[item]];
-        run_range<T, MEXP, SYM, TPW>(a, d, mem, gtid, 1 + g, 0, (long long)a.nsweeps * d.n, true);
+        const long long total = (long long)a.nsweeps * d.n;
+        if (a.gmem)
+            run_range<T, MEXP, SYM, TPW, true>(a, d, mem, gtid, 1 + g, 0, total, true);
+        else
+            run_range<T, MEXP, SYM, TPW, false>(a, d, mem, gtid, 1 + g, 0, total, true);
         return;
     }
     // persistent: take ready walkers from the FIFO, advance each by one chunk, put it back
@@ -1046,7 +1146,9 @@ __global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_ker
         const long long m0 = (long long)(c & (DEAD - 1)) * a.chunk_moves;
         const long long m1 = min(total, m0 + a.chunk_moves);
         bool ok = true;
-        if (!(c & DEAD)) ok = run_range<T, MEXP, SYM, TPW>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total);
+        if (!(c & DEAD))
+            ok = a.gmem ? run_range<T, MEXP, SYM, TPW, true>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total)
+                        : run_range<T, MEXP, SYM, TPW, false>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total);
         __threadfence();  // this thread's stores of the walker state, before it is handed on
         group_sync<TPW>(1 + g);
         if (gtid == 0) {
@@ -1167,7 +1269,8 @@ __global__ void __launch_bounds__(TPW) trial_kernel(PassArgs a)
         const T bx[1] = {wrap(ax[0] + (T)a.delta[3 * mi], L)}, by[1] = {wrap(ay[0] + (T)a.delta[3 * mi + 1], L)},
                 bz[1] = {wrap(az[0] + (T)a.delta[3 * mi + 2], L)};
         T S[1];
-        batch_partners<T, MEXP, SYM, TPW, 1>(J, sx, sy, sz, d.n, nv, s1, ax, ay, az, bx, by, bz, S, nullptr, gtid);
+        batch_partners<T, MEXP, SYM, TPW, 1, true>(J, sx, sy, sz, d.n, nv, s1, ax, ay, az, bx, by, bz, S, nullptr,
+                                                  gtid);
         const T delta = group_sum<TPW>(S[0], redT, phT, 1, gtid);
         if (gtid == 0) a.out[mi] = (double)delta;
     }
