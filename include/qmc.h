@@ -158,6 +158,18 @@ int qmc_trial_delta(const qmc_walker_desc *d, int W, const qmc_options *opt, con
                     const int32_t *s, const double *delta, int M, double *out, void *stream);
 
 /*
+ * qmc_pair_hist -- pair-distance histogram of each configuration, the data of the pair
+ * distribution function g(r) (the paper's analysis, Sec. 5.4 and Sec. 7.1).
+ *   hist  [W*nbins] device uint64, added to: the number of pairs i < j whose minimum-image
+ *         distance r satisfies r < rmax, in bin floor(r * nbins / rmax).
+ *   nbins 1..16384; rmax > 0 (normally <= L/2).  Counts are exact integers; in FP64 the distance
+ *         is computed as sqrt((dx*dx + dy*dy) + dz*dz) without fused operations.
+ * g(r) of bin k is its count divided by samples * n(n-1)/2 * (4 pi / 3)(r_{k+1}^3 - r_k^3) / L^3.
+ */
+int qmc_pair_hist(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos, int nbins,
+                  double rmax, uint64_t *hist, void *stream);
+
+/*
  * qmc_autotune -- time qmc_sweep on a scratch copy of `pos` for each admissible
  * threads-per-walker choice and remember the fastest for batches of this shape (largest n,
  * W, precision, exponent); later calls with threads_per_walker = 0 use it.  Synchronises the

@@ -90,6 +90,8 @@ def lib():
             L.orc_run_batch.argtypes = [C.c_int, C.POINTER(Walker), C.POINTER(C.c_int64), _D, _D, _D, _D,
                                         C.POINTER(C.c_uint64), C.c_int, C.c_int, _D, C.c_int]
             L.orc_run_batch.restype = C.c_int
+            L.orc_pair_hist.argtypes = [C.c_int, _D, _D, _D, C.c_double, C.c_int, C.c_double,
+                                        C.POINTER(C.c_uint64)]
             L.orc_sizeof_walker.restype = C.c_int
             assert L.orc_sizeof_walker() == C.sizeof(Walker), "orc_walker_t layout mismatch"
             _lib = L
@@ -167,6 +169,15 @@ def trial_delta(pos, L, b, m, sym, s, delta):
     d = lib().orc_trial_delta(p.shape[1], _dp(p[0]), _dp(p[1]), _dp(p[2]), L, b, m, sym, int(s),
                               float(delta[0]), float(delta[1]), float(delta[2]), _dp(npos))
     return d, npos
+
+
+def pair_hist(pos, L, nbins, rmax):
+    """Counts of pairs i < j with r < rmax in nbins equal bins."""
+    p = _xyz(pos)
+    out = np.zeros(nbins, dtype=np.uint64)
+    lib().orc_pair_hist(p.shape[1], _dp(p[0]), _dp(p[1]), _dp(p[2]), L, nbins, rmax,
+                        out.ctypes.data_as(C.POINTER(C.c_uint64)))
+    return out
 
 
 def move_randoms(seed, wid, proposal, sequential, n, t, k, step):

@@ -345,6 +345,24 @@ ORC_API double orc_trial_delta(int n, const double *x, const double *y, const do
     return sum;
 }
 
+/* Pair-distance histogram (the paper's g(r) analysis, Sec. 5.4): pairs i < j with r < rmax,
+ * bin floor(r nbins / rmax); counts added to out[nbins].                                      */
+ORC_API void orc_pair_hist(int n, const double *x, const double *y, const double *z, double L, int nbins,
+                           double rmax, uint64_t *out)
+{
+    double d[3];
+    const double scale = (double)nbins / rmax;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            double r = pair_dist(x, y, z, i, j, L, d);
+            if (r < rmax) {
+                int b = (int)(r * scale);
+                if (b > nbins - 1) b = nbins - 1;
+                out[b] += 1;
+            }
+        }
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Random numbers of one move: particle s, displacement delta, dice xi                         */
 /* ------------------------------------------------------------------------------------------ */

@@ -22,7 +22,7 @@ from . import build as _build
 __all__ = [
     "QMC_FP32", "QMC_FP64", "QMC_CUBE", "QMC_GAUSS", "QmcError", "WalkerDesc", "Options", "lib", "descs",
     "options", "qmc_init_walkers", "qmc_sweep", "qmc_local_energy", "qmc_energy_grad", "qmc_log_psi",
-    "qmc_trial_delta", "qmc_sweep_static", "QMC_STATIC_MAX_WALKERS", "qmc_autotune", "qmc_capacity", "qmc_status", "qmc_launch_count", "qmc_version",
+    "qmc_trial_delta", "qmc_pair_hist", "pair_correlation", "qmc_sweep_static", "QMC_STATIC_MAX_WALKERS", "qmc_autotune", "qmc_capacity", "qmc_status", "qmc_launch_count", "qmc_version",
     "qmc_shutdown", "Batch", "QmcGrad", "ACCUM_FIELDS", "ENERGY_FIELDS", "GRAD_FIELDS",
 ]
 
@@ -78,6 +78,7 @@ def lib():
         L.qmc_log_psi.argtypes = [D, C.c_int, O, _VP, _VP, _VP]
         L.qmc_trial_delta.argtypes = [D, C.c_int, O, _VP, _VP, _VP, C.c_int, _VP, _VP]
         L.qmc_autotune.argtypes = [D, C.c_int, O, _VP, _VP, C.POINTER(C.c_int)]
+        L.qmc_pair_hist.argtypes = [D, C.c_int, O, _VP, C.c_int, C.c_double, _VP, _VP]
         L.qmc_sweep_static.argtypes = [D, C.c_int, O, _VP, _VP, _VP, C.c_uint64, C.c_int, C.c_int, _VP, _VP, _VP]
         L.qmc_capacity.argtypes = [C.c_int]
         L.qmc_status.argtypes = [_VP, C.c_int, C.POINTER(C.c_uint32)]
@@ -167,6 +168,20 @@ def qmc_log_psi(d, opt, pos, out, stream=None):
 def qmc_trial_delta(d, opt, pos, s, delta, M, out, stream=None):
     return _check(lib().qmc_trial_delta(d, len(d), C.byref(opt), _ptr(pos), _ptr(s), _ptr(delta), M, _ptr(out),
                                         _stream(stream)))
+
+
+def qmc_pair_hist(d, opt, pos, nbins, rmax, hist, stream=None):
+    return _check(lib().qmc_pair_hist(d, len(d), C.byref(opt), _ptr(pos), nbins, rmax, _ptr(hist), _stream(stream)))
+
+
+def pair_correlation(counts, n, L, rmax, samples):
+    """g(r) from summed pair counts (qmc_pair_hist) of `samples` configurations of n atoms in a
+    cube of side L: counts over the ideal-gas expectation of each spherical shell."""
+    counts = np.asarray(counts, dtype=np.float64)
+    nb = counts.shape[-1]
+    edges = np.linspace(0.0, rmax, nb + 1)
+    shell = 4.0 * np.pi / 3.0 * (edges[1:] ** 3 - edges[:-1] ** 3) / L ** 3
+    return 0.5 * (edges[1:] + edges[:-1]), counts / (samples * n * (n - 1) / 2.0 * shell)
 
 
 def qmc_autotune(d, opt, pos, stream=None) -> int:

@@ -557,6 +557,39 @@ int qmc_energy_grad(const qmc_walker_desc *d, int W, const qmc_options *opt, con
     return pass_impl(d, W, opt, pos, out, 3, nullptr, nullptr, 0, (cudaStream_t)stream);
 }
 
+int qmc_pair_hist(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos, int nbins, double rmax,
+                  uint64_t *hist, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if ((rc = check_ptr(pos, "pos", 16)) || (rc = check_ptr(hist, "hist", 8))) return rc;
+    if (nbins < 1 || nbins > 16384) return fail(QMC_ERR_ARG, "nbins must be in 1..16384");
+    if (!is_fin(rmax) || rmax <= 0) return fail(QMC_ERR_ARG, "rmax must be finite and > 0");
+    Prep p;
+    if ((rc = prepare(d, W, opt, st, p))) return rc;
+    const Plan &P = *p.plan;
+    const Shape sh = shape_of(P, opt->precision, PASS_TPW, 1, false);
+    PassArgs a;
+    a.walkers = P.d_walkers;
+    a.W = W;
+    a.stride = sh.stride;
+    a.tile = 0;
+    a.gmem = sh.gmem;
+    a.pos = pos;
+    a.out = nullptr;
+    a.h2m = opt->hbar2_over_m;
+    a.s = nullptr;
+    a.delta = nullptr;
+    a.M = 0;
+    a.err = p.ds->err;
+    const size_t smem = sh.smem + sizeof(unsigned) * (size_t)nbins;
+    if (smem > MAX_SMEM) return fail(QMC_ERR_CAPACITY, "histogram does not fit shared memory next to the walker");
+    cudaError_t e = launch_hist(opt->precision, W, smem, st, a, nbins, rmax, reinterpret_cast<unsigned long long *>(hist));
+    if (e != cudaSuccess) return cuda_fail(e, "histogram launch");
+    g_launches.fetch_add(1);
+    return QMC_OK;
+}
+
 int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos, void *stream,
                  int *tpw_out)
 {

@@ -62,6 +62,29 @@ cudaError_t launch_pass(int precision, Variant v, int kind, int grid, size_t sme
                                  : pass_t<float>(v, kind, grid, smem, st, a);
 }
 
+cudaError_t launch_hist(int precision, int grid, size_t smem, cudaStream_t st, const PassArgs &a, int nbins,
+                        double rmax, unsigned long long *hist)
+{
+    if (precision == QMC_FP64) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = big_smem(hist_kernel<double, PASS_TPW>);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        hist_kernel<double, PASS_TPW><<<grid, PASS_TPW, smem, st>>>(a, nbins, rmax, hist);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = big_smem(hist_kernel<float, PASS_TPW>);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        hist_kernel<float, PASS_TPW><<<grid, PASS_TPW, smem, st>>>(a, nbins, rmax, hist);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init(int precision, int grid, size_t smem, cudaStream_t st, const DevWalker *walkers,
                         unsigned long long seed, double sigma, void *pos)
 {

@@ -1277,6 +1277,71 @@ __global__ void __launch_bounds__(TPW) trial_kernel(PassArgs a)
 }
 
 // ----------------------------------------------------------------------------------------------
+// Pair-distance histogram (the paper's g(r) analysis, Sec. 5.4 and Sec. 7.1): counts of pairs
+// i < j with r < rmax in nbins equal bins, bin = floor(r nbins / rmax), added to hist[walker].
+// Counts are integers (the shared-memory atomics commute), so the result is exact.  In FP64
+// the squared distance is summed unfused in x, y, z order, as the oracle does.
+// ----------------------------------------------------------------------------------------------
+template <typename T, int TPW>
+__global__ void __launch_bounds__(TPW) hist_kernel(PassArgs a, int nbins, double rmax, unsigned long long *hist)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    GroupMem<T> mem;
+    mem.bind(smem, a.stride, TPW, false);
+    unsigned *counts = reinterpret_cast<unsigned *>(smem + group_smem<T>(a.stride, TPW, false));
+    T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
+    const DevWalker d = a.walkers[blockIdx.x];
+    const int gtid = threadIdx.x;
+    int phT = 0;
+    constexpr int VN = Vec<T>::N;
+    using V = typename Vec<T>::type;
+    const T *gx = reinterpret_cast<const T *>(a.pos) + d.off;
+    const T L = (T)d.L, iL = (T)1 / L;
+    if (a.gmem) {
+        mem.use_global(const_cast<T *>(gx), d.pad);
+        sx = mem.sx;
+        sy = mem.sy;
+        sz = mem.sz;
+    }
+    if (!(a.gmem ? check_walker<T, TPW>(gx, d.n, d.pad, L, redT, phT, 1, gtid)
+                 : load_walker<T, TPW>(gx, d.n, d.pad, a.stride, L, sx, sy, sz, redT, phT, 1, gtid))) {
+        if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
+        return;
+    }
+    for (int b = gtid; b < nbins; b += TPW) counts[b] = 0u;
+    __syncthreads();
+    const int n = d.n, nv = (n + VN - 1) / VN;
+    const T r2max = (T)(rmax * rmax), scale = (T)((double)nbins / rmax);
+    for (int i = gtid; i < n; i += TPW) {
+        const T xi = sx[i], yi = sy[i], zi = sz[i];
+        for (int c = 0; c < nv; ++c) {
+            const V X = reinterpret_cast<const V *>(sx)[c];
+            const V Y = reinterpret_cast<const V *>(sy)[c];
+            const V Z = reinterpret_cast<const V *>(sz)[c];
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const int j = c * VN + e;
+                const T dx = mi_signed(xi - Vec<T>::get(X, e), L, iL);
+                const T dy = mi_signed(yi - Vec<T>::get(Y, e), L, iL);
+                const T dz = mi_signed(zi - Vec<T>::get(Z, e), L, iL);
+                T r2;
+                if constexpr (std::is_same<T, double>::value)
+                    r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                else
+                    r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (j > i && j < n && r2 < r2max) {
+                    const int bin = min(nbins - 1, (int)(sqrt(r2) * scale));
+                    atomicAdd(&counts[bin], 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    unsigned long long *h = hist + (size_t)d.slot * nbins;
+    for (int b = gtid; b < nbins; b += TPW) h[b] += counts[b];
+}
+
+// ----------------------------------------------------------------------------------------------
 // ln psi, E_L and their (b, m) derivatives.  u depends on b only through c = -b^m/2, so
 // d/db of ln psi, u', u'' is (dc/db)/c = m/b times the quantity; the m-derivatives use
 // d f/dm = f ln(b/r) (and the matching forms for f', f'').

@@ -36,6 +36,8 @@ constexpr int TRIAL_TPW = 128;  // threads per walker of qmc_trial_delta
 // kind 0: local energy, 1: ln psi, 2: trial deltas, 3: energy + (b, m) gradient
 cudaError_t launch_pass(int precision, Variant v, int kind, int grid, size_t smem, cudaStream_t st,
                         const PassArgs &a);
+cudaError_t launch_hist(int precision, int grid, size_t smem, cudaStream_t st, const PassArgs &a, int nbins,
+                        double rmax, unsigned long long *hist);
 cudaError_t launch_init(int precision, int grid, size_t smem, cudaStream_t st, const DevWalker *walkers,
                         unsigned long long seed, double sigma, void *pos);
 

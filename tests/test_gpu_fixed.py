@@ -154,3 +154,50 @@ def test_nonfinite_coordinates_are_flagged_not_faulted():
     assert not torch.equal(host[:3 * 64], before[:3 * 64].cpu())       # walker 0 moved
     assert torch.equal(host[r.offset + 6:r.offset + 3 * 64], before[r.offset + 6:r.offset + 3 * 64].cpu())
     assert sw.cpu().tolist() == [2, 0]
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_pair_histogram(prec):
+    ns = [2, 17, 64, 130, 512]
+    P = lattice_batch(ns, prec, seed=80)
+    nbins = 64
+    hist = zeros((P.W, nbins), torch.int64)
+    rmax = [L / 2 for L in P.Ls]
+    # one call per walker because rmax differs; the second call on the same rows adds
+    for w in range(P.W):
+        one = q.descs([tuple(getattr(P.d[w], f) for f, _ in q.WalkerDesc._fields_)])
+        one[0].offset = 0
+        r = P.d[w]
+        sub = P.pos[r.offset:r.offset + 3 * r.pad_n].contiguous()
+        q.qmc_pair_hist(one, q.options(precision=prec), sub, nbins, rmax[w], hist[w])
+        q.qmc_pair_hist(one, q.options(precision=prec), sub, nbins, rmax[w], hist[w])
+    got = hist.cpu().numpy()
+    for w in range(P.W):
+        want = 2 * oracle.pair_hist(P.confs[w], P.Ls[w], nbins, rmax[w]).astype(np.int64)
+        if prec == q.QMC_FP64:
+            assert np.array_equal(got[w], want)
+        else:
+            # FP32 distances may put a pair near a bin edge into the neighbouring bin
+            assert abs(int(got[w].sum()) - int(want.sum())) <= 4
+            assert np.abs(got[w] - want).sum() <= 8 + want.sum() // 2000
+
+
+def test_pair_correlation_of_a_liquid():
+    n, W = 512, 64
+    L = qi.box_side(n, qi.RHO_HE)
+    pad = qi.pad4(n)
+    d = q.descs([(n, pad, w * 3 * pad, w, L, 0.0, qi.B_HE, 5.0, 0.8) for w in range(W)])
+    opt = q.options()
+    pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
+    q.qmc_init_walkers(d, 21, 0.1, opt, pos)
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    q.qmc_sweep(d, opt, pos, lp, sw, 21, 300, 0, acc)
+    nbins, rmax = 70, L / 2
+    hist = zeros((W, nbins), torch.int64)
+    for _ in range(10):
+        q.qmc_sweep(d, opt, pos, lp, sw, 21, 5, 0, acc)
+        q.qmc_pair_hist(d, opt, pos, nbins, rmax, hist)
+    r, g = q.pair_correlation(hist.sum(0).cpu().numpy(), n, L, rmax, 10 * W)
+    assert np.all(g[r < 1.8] == 0.0)           # hard core of the Jastrow factor
+    assert 1.2 < g.max() < 1.8 and 3.0 < r[np.argmax(g)] < 4.0   # first shell of liquid 4He
+    assert abs(g[(r > 9) & (r < 12)].mean() - 1.0) < 0.05

@@ -348,3 +348,16 @@ def test_init_walker_fcc_subset():
     assert np.sqrt((d ** 2).sum(-1)).min(axis=1).max() < 6 * sigma * math.sqrt(3)
     other = oracle.init_walker(n, L, 0x5EED0001, 1, sigma)
     assert not np.array_equal(pos, other)
+
+
+def test_pair_histogram_by_brute_force_images():
+    n, L = 40, 9.0
+    pos = qi.uniform_positions(n, L, 12)
+    nbins, rmax = 30, 4.5
+    got = oracle.pair_hist(pos, L, nbins, rmax)
+    want = np.zeros(nbins, dtype=np.uint64)
+    for _, _, r in _brute_pairs(pos, L):
+        if r < rmax:
+            want[min(nbins - 1, int(r * nbins / rmax))] += 1
+    assert np.array_equal(got, want)
+    assert got.sum() <= n * (n - 1) // 2
