@@ -437,12 +437,14 @@ def run_uneven(args):
 
 
 def run_large(args):
-    """N = 10000 at 0.02186 A^-3, one walker per SM, FP32; a step = 20 sweeps then the adjoint
-    (ln psi, E_L and their (b, m) derivatives) of every walker."""
+    """N = --large-n (default 10000; 40960 is the paper's largest system, Sec. 7.4) at
+    0.02186 A^-3, one walker per SM, FP32; a step = --large-sweeps sweeps (default 20) then the adjoint (ln psi, E_L and
+    their (b, m) derivatives) of every walker.  Walkers beyond one CTA's shared memory run from
+    HBM (L2-resident at these sizes)."""
     import torch
     import paper_1312_1282_gb300 as q
     torch.cuda.set_device(0)
-    n = 10000
+    n, S = args.large_n, args.large_sweeps
     W = torch.cuda.get_device_properties(0).multi_processor_count
     L = qi.box_side(n, qi.RHO_HE)
     pad = qi.pad4(n)
@@ -467,7 +469,7 @@ def run_large(args):
         a, b = _events(torch)
         c, e = _events(torch)
         a.record()
-        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, 20, 20, acc)
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, S, S, acc)
         b.record()
         c.record()
         q.qmc_energy_grad(d, opt, pos, grad)
@@ -481,10 +483,11 @@ def run_large(args):
     EL, Ob, Om = g[:, 1], g[:, 2], g[:, 3]
     dE_db = 2 * (np.mean(EL * Ob) - EL.mean() * Ob.mean()) / n
     dE_dm = 2 * (np.mean(EL * Om) - EL.mean() * Om.mean()) / n
-    pe = 2.0 * n * (n - 1) * W * 20 * args.steps
-    print(json.dumps({"config": "N=10000, one walker per SM, 20 sweeps + adjoint per step", "walkers": W,
-                      "threads_per_walker": tpw, "pair_evals_per_s": pe / (t_sw * 1e-3),
-                      "ms_per_20_sweeps": t_sw / args.steps, "ms_per_adjoint": t_gr / args.steps,
+    pe = 2.0 * n * (n - 1) * W * S * args.steps
+    print(json.dumps({"config": f"N={n}, one walker per SM, {S} sweeps + adjoint per step", "walkers": W,
+                      "hbm_walkers": n > q.qmc_capacity(q.QMC_FP32), "threads_per_walker": tpw,
+                      "pair_evals_per_s": pe / (t_sw * 1e-3), "ms_per_macroupdate_all_walkers": t_sw / args.steps / S,
+                      "ms_per_step_sweeps": t_sw / args.steps, "ms_per_adjoint": t_gr / args.steps,
                       "E_per_atom": float(acc[:, 0].sum() / acc[:, 6].sum() / n),
                       "dE_per_atom_db_K_per_A": dE_db, "dE_per_atom_dm": dE_dm}), flush=True)
     return 0
@@ -532,6 +535,99 @@ def run_fp64cmp(args):
     return 0
 
 
+T2E_SIZES = (128, 256, 512, 1000, 2000, 4000)
+
+
+def run_t2e(args):
+    """Time to error (the paper's full-acceleration benchmark, Sec. 7.3): for each N, the error
+    sigma of E/N after t seconds of sampling, with the on-GPU local energy taken every m
+    macroupdates and m from Eq. optimalCPU (generation and analysis on the same unit).
+    Per N: W walkers (8192 / N per SM, 2 to 16), Gaussian moves of RMS 0.5 rho^(-1/3) (Sec. 7),
+    300 equilibration sweeps; t_G and t_A from CUDA events around 40-sweep launches without and
+    with the energy every sweep; m_c from 400 per-sweep samples of every walker (Sokal window);
+    then a production run of --t2e-seconds at the optimal m and one at m = 1.  sigma is the
+    spread of the W independent chain means / sqrt(W); t sigma^2 is reported in s mK^2."""
+    import torch
+    import paper_1312_1282_gb300 as q
+    from paper_1312_1282_gb300 import analysis as an
+    torch.cuda.set_device(0)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    sizes = [int(v) for v in args.t2e_sizes.split(",")] if args.t2e_sizes else list(T2E_SIZES)
+    rows = []
+    for n in sizes:
+        W = nsm * max(2, min(16, 8192 // n))
+        L = qi.box_side(n, qi.RHO_HE)
+        pad = qi.pad4(n)
+        sigma = 0.5 * qi.RHO_HE ** (-1.0 / 3.0) / math.sqrt(3.0)  # per component
+        d = q.descs([(n, pad, w * 3 * pad, w, L, 0.0, qi.B_HE, 5.0, sigma) for w in range(W)])
+        opt = q.options(precision=q.QMC_FP32, proposal=q.QMC_GAUSS, recompute_every=50)
+        pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
+        lp = torch.zeros(W, dtype=torch.float64, device="cuda")
+        sw = torch.zeros(W, dtype=torch.int64, device="cuda")
+        acc = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+        seed = 0x5EED0006 + n
+        q.qmc_init_walkers(d, seed, 0.1, opt, pos)
+        q.qmc_log_psi(d, opt, pos, lp)
+        tpw = q.qmc_autotune(d, opt, pos)
+        q.qmc_sweep(d, opt, pos, lp, sw, seed, 300, 0, acc)
+        torch.cuda.synchronize()
+
+        def timed(nsw, every):
+            a, b = _events(torch)
+            a.record()
+            q.qmc_sweep(d, opt, pos, lp, sw, seed, nsw, every, acc)
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) * 1e-3
+
+        timed(10, 1)  # warm
+        t_G = timed(40, 0) / 40
+        t_A = max(timed(40, 1) / 40 - t_G, 1e-9)
+        alpha = t_A / t_G
+        S = 400
+        series = torch.empty(W, S, dtype=torch.float64, device="cuda")
+        for k in range(S):
+            acc.zero_()
+            q.qmc_sweep(d, opt, pos, lp, sw, seed, 1, 1, acc)
+            series[:, k] = acc[:, 0]
+        ser = series.cpu().numpy() / n
+        m_c = an.autocorr_time(ser)
+        plateau = max(r for _, r in an.reblocking(ser))
+        sigma0 = float(ser.var(axis=1, ddof=1).mean() ** 0.5)
+        m_opt = an.integer_m(an.optimal_m_sequential(m_c, alpha), m_c, t_G, t_A)
+        res = {"N": n, "walkers": W, "threads_per_walker": tpw, "t_G_ms": t_G * 1e3, "t_A_ms": t_A * 1e3,
+               "alpha": alpha, "m_c": m_c, "reblocking_plateau": plateau, "sigma0_mK": sigma0 * 1e3, "m_opt": m_opt,
+               "predicted_penalty_m1": an.time_per_error(1, m_c, t_G, t_A) / an.time_per_error(m_opt, m_c, t_G, t_A)}
+        for tag, m in (("opt", m_opt), ("m1", 1)):
+            chunk = m * max(1, 50 // m)
+            nchunks = max(1, math.ceil(args.t2e_seconds / ((t_G + t_A / m) * chunk)))
+            acc.zero_()
+            torch.cuda.synchronize()
+            a, b = _events(torch)
+            a.record()
+            for _ in range(nchunks):
+                q.qmc_sweep(d, opt, pos, lp, sw, seed, chunk, m, acc)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) * 1e-3
+            e = (acc[:, 0] / acc[:, 6] / n).cpu().numpy()
+            err = float(e.std(ddof=1) / math.sqrt(W))
+            res[tag] = {"m": m, "sweeps": nchunks * chunk, "seconds": t, "E_per_atom": float(e.mean()),
+                        "sigma_mK": err * 1e3, "t_sigma2_s_mK2": t * (err * 1e3) ** 2,
+                        "acceptance": float(acc[:, 7].sum().item() / (W * n * nchunks * chunk))}
+        res["t_to_1mK_s"] = res["opt"]["t_sigma2_s_mK2"]
+        res["measured_penalty_m1"] = res["m1"]["t_sigma2_s_mK2"] / res["opt"]["t_sigma2_s_mK2"]
+        assert q.qmc_status(None, 600000) == 0
+        rows.append(res)
+        print(json.dumps(res), flush=True)
+        del pos, lp, sw, acc, series
+    print(json.dumps({"config": "time to error, E/N of liquid 4He, FP32, Gaussian moves, m from Eq. optimalCPU",
+                      "t_sigma2_s_mK2_by_N": {str(r["N"]): r["opt"]["t_sigma2_s_mK2"] for r in rows},
+                      "t_sigma2_per_atom_s_mK2": {str(r["N"]): r["opt"]["t_sigma2_s_mK2"] / r["N"] for r in rows}}),
+          flush=True)
+    return 0
+
+
 def _kernel_hash():
     import hashlib
     h = hashlib.sha1()
@@ -550,7 +646,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--equil", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
-    ap.add_argument("--config", default="headline", choices=["headline", "uneven", "large", "fp64cmp"],
+    ap.add_argument("--large-n", type=int, default=10000, help="large: atoms per walker")
+    ap.add_argument("--large-sweeps", type=int, default=20, help="large: sweeps per step")
+    ap.add_argument("--t2e-seconds", type=float, default=3.0, help="t2e: production seconds per N and m")
+    ap.add_argument("--t2e-sizes", default="", help="t2e: comma-separated N (default 128..4000)")
+    ap.add_argument("--config", default="headline", choices=["headline", "uneven", "large", "fp64cmp", "t2e"],
                     help="headline: the benchmark line; the others measure the other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -563,6 +663,8 @@ def main():
         return run_large(args)
     if args.config == "fp64cmp":
         return run_fp64cmp(args)
+    if args.config == "t2e":
+        return run_t2e(args)
     return run_native(args)
 
 
