@@ -38,9 +38,10 @@ N_ATOMS, WALKERS, SWEEPS_PER_STEP = 1952, 528, 5
 METRIC = "pair evals/s and sweeps/s at N=1952, FP32-batched vs FP64 plain, E/atom within 2σ"
 WORKLOAD = "VMC liquid 4He N=1952 rho=0.02186 b=3.07 m=5 Aziz-II, 528 walkers, 5 sweeps + 1 local energy per step"
 # FP32 operations per pair evaluation of a move (difference 3, image fold 6, r^2 3, clamp 1,
-# r and L - r 2, fifth powers 6, u 2, accumulation 1) and per unordered pair of the local-energy
-# pass (71); the op lists are in the design doc.  SFU operations (2 and 3-4) are not counted.
-C_PAIR = 24.0
+# r and L - r 2, q^2 q^4 w^2 w^4 4, two fused multiply-accumulates 2) and per unordered pair of
+# the local-energy pass (71); the op lists are in the design doc.  SFU operations (2 and 3-4) are not
+# counted.
+C_PAIR = 21.0
 C_ENERGY = 71.0
 FP32_LANES_PER_SM = 128
 

@@ -255,18 +255,18 @@ __device__ void store_walker(T *gx, int n, int pad, const T *sx, const T *sy, co
 }
 
 // ----------------------------------------------------------------------------------------------
-// Eq. (JastrowUpdate) terms u(|r' - r_j|) - u(|r_s - r_j|), FP32, exponent 5, symmetrised u:
-// two partners per packed f32x2 instruction (FFMA2/FADD2/FMUL2 issue once for two lanes of
-// work; min/max and the SFU stay scalar).
+// Partner sums of Eq. (JastrowUpdate), FP32, exponent 5, symmetrised u: with q = 1/r and
+// w = 1/(L - r), r clamped at L/2, u(r) = c (q^5 + w^5) - K (Eqs. uFunction, fifthPower), so
+// sum_j [u(r'_j) - u(r_j)] = c (sum_j [q'^5 + w'^5] - sum_j [q^5 + w^5]).  Two partners per
+// packed f32x2 instruction (FFMA2/FADD2/FMUL2 issue once for two lanes of work; min/max and the
+// SFU stay scalar).
 struct Packed5 {
-    float2 L, hL2, m1, c, nK;  // (L, L), ((L/2)^2, ...), (-1, -1), (c, c), (-K, -K)
+    float2 L, hL2, m1;  // (L, L), ((L/2)^2, ...), (-1, -1)
     __device__ __forceinline__ void init(const Jas<float, 5, true> &J)
     {
         L = make_float2(J.L, J.L);
         hL2 = make_float2(J.hL2, J.hL2);
         m1 = make_float2(-1.f, -1.f);
-        c = make_float2(J.c, J.c);
-        nK = make_float2(-J.K, -J.K);
     }
     // |d| folded to the nearest image: min(|d|, L - |d|), for two differences at once
     __device__ __forceinline__ float2 fold(float2 d) const
@@ -275,8 +275,9 @@ struct Packed5 {
         const float2 b = __ffma2_rn(a, m1, L);
         return make_float2(fminf(a.x, b.x), fminf(a.y, b.y));
     }
-    // u(r) of two partners from their coordinate differences (clamped at r = L/2)
-    __device__ __forceinline__ float2 u(float2 dx, float2 dy, float2 dz) const
+    // acc += q^5 + w^5 of two partners, i.e. (u(r) + K) / c: the constant and the factor c are
+    // applied once per partner sum, and the last power of each term is fused into the add
+    __device__ __forceinline__ void acc5(float2 dx, float2 dy, float2 dz, float2 &acc) const
     {
         const float2 mx = fold(dx), my = fold(dy), mz = fold(dz);
         float2 r2 = __fmul2_rn(mx, mx);
@@ -288,8 +289,8 @@ struct Packed5 {
         const float2 w = __ffma2_rn(r, m1, L);
         const float2 iw = make_float2(rcp_a(w.x), rcp_a(w.y));
         const float2 q2 = __fmul2_rn(q, q), w2 = __fmul2_rn(iw, iw);
-        const float2 q5 = __fmul2_rn(__fmul2_rn(q2, q2), q), w5 = __fmul2_rn(__fmul2_rn(w2, w2), iw);
-        return __ffma2_rn(c, q5, __ffma2_rn(c, w5, nK));
+        acc = __ffma2_rn(__fmul2_rn(q2, q2), q, acc);
+        acc = __ffma2_rn(__fmul2_rn(w2, w2), iw, acc);
     }
 };
 
@@ -709,7 +710,7 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
     if constexpr (std::is_same<T, float>::value && MEXP == 5 && SYM) {
         Packed5 P;
         P.init(J);
-        float2 nax[K], nay[K], naz[K], nbx[K], nby[K], nbz[K], acc[K];
+        float2 nax[K], nay[K], naz[K], nbx[K], nby[K], nbz[K], acco[K], accn[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             nax[i] = make_float2(-ax[i], -ax[i]);
@@ -718,7 +719,8 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
             nbx[i] = make_float2(-bx[i], -bx[i]);
             nby[i] = make_float2(-by[i], -by[i]);
             nbz[i] = make_float2(-bz[i], -bz[i]);
-            acc[i] = make_float2(0.f, 0.f);
+            acco[i] = make_float2(0.f, 0.f);
+            accn[i] = make_float2(0.f, 0.f);
         }
 #pragma unroll 2
         for (int c = gtid; c < nv; c += TPW) {
@@ -746,16 +748,16 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
             const float2 za = make_float2(Z.x, Z.y), zb = make_float2(Z.z, Z.w);
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-                const float2 oa = P.u(__fadd2_rn(xa, nax[i]), __fadd2_rn(ya, nay[i]), __fadd2_rn(za, naz[i]));
-                const float2 na = P.u(__fadd2_rn(xa, nbx[i]), __fadd2_rn(ya, nby[i]), __fadd2_rn(za, nbz[i]));
-                const float2 ob = P.u(__fadd2_rn(xb, nax[i]), __fadd2_rn(yb, nay[i]), __fadd2_rn(zb, naz[i]));
-                const float2 nb = P.u(__fadd2_rn(xb, nbx[i]), __fadd2_rn(yb, nby[i]), __fadd2_rn(zb, nbz[i]));
-                acc[i] = __fadd2_rn(acc[i], __ffma2_rn(oa, P.m1, na));
-                acc[i] = __fadd2_rn(acc[i], __ffma2_rn(ob, P.m1, nb));
+                P.acc5(__fadd2_rn(xa, nax[i]), __fadd2_rn(ya, nay[i]), __fadd2_rn(za, naz[i]), acco[i]);
+                P.acc5(__fadd2_rn(xa, nbx[i]), __fadd2_rn(ya, nby[i]), __fadd2_rn(za, nbz[i]), accn[i]);
+                P.acc5(__fadd2_rn(xb, nax[i]), __fadd2_rn(yb, nay[i]), __fadd2_rn(zb, naz[i]), acco[i]);
+                P.acc5(__fadd2_rn(xb, nbx[i]), __fadd2_rn(yb, nby[i]), __fadd2_rn(zb, nbz[i]), accn[i]);
             }
         }
+        // every partner (the masked ones at the clamp included) is in both sums, so the constants
+        // K cancel: S = c (sum_new - sum_old)
 #pragma unroll
-        for (int i = 0; i < K; ++i) S[i] = acc[i].x + acc[i].y;
+        for (int i = 0; i < K; ++i) S[i] = J.c * ((accn[i].x + accn[i].y) - (acco[i].x + acco[i].y));
     } else {
 #pragma unroll 2
         for (int c = gtid; c < nv; c += TPW) {
