@@ -44,6 +44,7 @@ WORKLOAD = "VMC liquid 4He N=1952 rho=0.02186 b=3.07 m=5 Aziz-II, 528 walkers, 5
 C_PAIR = 21.0
 C_ENERGY = 71.0
 FP32_LANES_PER_SM = 128
+SFU_PAIR, SFU_ENERGY, SFU_LANES_PER_SM = 2.0, 3.0, 16
 
 
 def pair_evals_per_sweep(n: int) -> float:
@@ -319,6 +320,11 @@ def run_native(args):
     peaks = _peaks()
     clk = clock.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak_tops = nsm * FP32_LANES_PER_SM * clk * 1e6 / 1e12
+    # the SFU (MUFU) co-limit: rsqrt and rcp per pair evaluation; rsqrt, rcp and ex2 per energy pair
+    # (the damping exponential, taken only where a lane needs it, is not counted)
+    sfu_launch = pe_step * SFU_PAIR + energy_pairs * SFU_ENERGY
+    sfu_achieved = sfu_launch / (total_ms / args.steps * 1e-3) / 1e12
+    sfu_peak = nsm * SFU_LANES_PER_SM * clk * 1e6 / 1e12
     ops_launch = pe_step * C_PAIR + energy_pairs * C_ENERGY
     achieved = ops_launch / (total_ms / args.steps * 1e-3) / 1e12
     traffic = None
@@ -361,7 +367,11 @@ def run_native(args):
                          "note": f"FP32-pipe lane ops ({C_PAIR:g}/pair eval, {C_ENERGY:g}/energy pair) vs "
                                  f"{nsm} SMs x 128 lanes x {clk:g} MHz",
                          "frac_at_median_clock": (achieved / (nsm * FP32_LANES_PER_SM * clock["sm_mhz"] * 1e-6)
-                                                  if clock.get("sm_mhz") else None)},
+                                                  if clock.get("sm_mhz") else None),
+                         "sfu": {"achieved": sfu_achieved, "peak": sfu_peak, "unit": "T ops/s",
+                                 "frac": sfu_achieved / sfu_peak,
+                                 "note": f"{SFU_PAIR:g}/pair eval, {SFU_ENERGY:g}/energy pair vs {nsm} SMs x "
+                                         f"{SFU_LANES_PER_SM} lanes x {clk:g} MHz"}},
             "clocks": clock,
         }
         if cpu:
@@ -542,12 +552,14 @@ T2E_SIZES = (128, 256, 512, 1000, 2000, 4000)
 def run_t2e(args):
     """Time to error (the paper's full-acceleration benchmark, Sec. 7.3): for each N, the error
     sigma of E/N after t seconds of sampling, with the on-GPU local energy taken every m
-    macroupdates and m from Eq. optimalCPU (generation and analysis on the same unit).
+    macroupdates (generation and analysis on the same unit, Eq. serialtime).
     Per N: W walkers (8192 / N per SM, 2 to 16), Gaussian moves of RMS 0.5 rho^(-1/3) (Sec. 7),
-    300 equilibration sweeps; t_G and t_A from CUDA events around 40-sweep launches without and
-    with the energy every sweep; m_c from 400 per-sweep samples of every walker (Sokal window);
-    then a production run of --t2e-seconds at the optimal m and one at m = 1.  sigma is the
-    spread of the W independent chain means / sqrt(W); t sigma^2 is reported in s mK^2."""
+    300 equilibration sweeps; for every thread-group size, t_G and the time per analysis step
+    t_step(m) = t_A + m t_G for m = 1, 2, 4 from CUDA events around 40-sweep launches; m_c from
+    400 per-sweep samples of every walker (Sokal window); the group size and m with the least
+    (1 + 2 m_c / m) t_step(m) (Eq. CorrelatedError), with Eq. optimalCPU's m from t_G and t_A
+    reported beside it; then a production run of --t2e-seconds at the chosen m and one at m = 1.
+    sigma is the spread of the W independent chain means / sqrt(W); t sigma^2 is in s mK^2."""
     import torch
     import paper_1312_1282_gb300 as q
     from paper_1312_1282_gb300 import analysis as an
@@ -569,22 +581,29 @@ def run_t2e(args):
         seed = 0x5EED0006 + n
         q.qmc_init_walkers(d, seed, 0.1, opt, pos)
         q.qmc_log_psi(d, opt, pos, lp)
-        tpw = q.qmc_autotune(d, opt, pos)
+        tpw_sweep = q.qmc_autotune(d, opt, pos)
         q.qmc_sweep(d, opt, pos, lp, sw, seed, 300, 0, acc)
         torch.cuda.synchronize()
 
-        def timed(nsw, every):
+        def timed(o, nsw, every):
             a, b = _events(torch)
             a.record()
-            q.qmc_sweep(d, opt, pos, lp, sw, seed, nsw, every, acc)
+            q.qmc_sweep(d, o, pos, lp, sw, seed, nsw, every, acc)
             b.record()
             torch.cuda.synchronize()
             return a.elapsed_time(b) * 1e-3
 
-        timed(10, 1)  # warm
-        t_G = timed(40, 0) / 40
-        t_A = max(timed(40, 1) / 40 - t_G, 1e-9)
-        alpha = t_A / t_G
+        # t_G for every admissible thread-group size, and the time per analysis step
+        # t_step(m) = t_A + m t_G measured directly for m = 1, 2, 4 (the energy sample changes
+        # which group size is fastest, and its cost inside a long launch depends on m)
+        shapes = {}
+        tpw = max(32, 1 << max(0, (n // 64 - 1).bit_length()))  # up to 64 partners per thread
+        while tpw <= min(1024, 4 * max(32, 1 << (max(1, (n + 3) // 4) - 1).bit_length())):
+            o = q.options(precision=q.QMC_FP32, proposal=q.QMC_GAUSS, recompute_every=50, threads_per_walker=tpw)
+            timed(o, 5, 1)  # warm
+            tg = timed(o, 40, 0) / 40
+            shapes[tpw] = (o, tg, {m: timed(o, 40, m) / 40 * m for m in (1, 2, 4)})
+            tpw *= 2
         S = 400
         series = torch.empty(W, S, dtype=torch.float64, device="cuda")
         for k in range(S):
@@ -595,13 +614,24 @@ def run_t2e(args):
         m_c = an.autocorr_time(ser)
         plateau = max(r for _, r in an.reblocking(ser))
         sigma0 = float(ser.var(axis=1, ddof=1).mean() ** 0.5)
-        m_opt = an.integer_m(an.optimal_m_sequential(m_c, alpha), m_c, t_G, t_A)
-        res = {"N": n, "walkers": W, "threads_per_walker": tpw, "t_G_ms": t_G * 1e3, "t_A_ms": t_A * 1e3,
-               "alpha": alpha, "m_c": m_c, "reblocking_plateau": plateau, "sigma0_mK": sigma0 * 1e3, "m_opt": m_opt,
-               "predicted_penalty_m1": an.time_per_error(1, m_c, t_G, t_A) / an.time_per_error(m_opt, m_c, t_G, t_A)}
+
+        def cost(k, m):  # time to unit error for unit sigma0 (Eq. CorrelatedError x t_step)
+            return (1.0 + 2.0 * m_c / m) * shapes[k][2][m]
+
+        tpw, m_opt = min(((k, m) for k in shapes for m in shapes[k][2]), key=lambda km: cost(*km))
+        opt, t_G, steps = shapes[tpw]
+        t_A = max(steps[1] - t_G, 1e-9)
+        alpha = t_A / t_G
+        m_model = an.integer_m(an.optimal_m_sequential(m_c, alpha), m_c, t_G, t_A)
+        res = {"N": n, "walkers": W, "threads_per_walker": tpw, "threads_per_walker_sweeps_only": tpw_sweep,
+               "shapes": {str(k): {"t_G_ms": v[1] * 1e3, "t_step_ms": {str(m): t * 1e3 for m, t in v[2].items()}}
+                          for k, v in shapes.items()},
+               "t_G_ms": t_G * 1e3, "t_A_ms": t_A * 1e3, "alpha": alpha, "m_c": m_c, "reblocking_plateau": plateau,
+               "sigma0_mK": sigma0 * 1e3, "m_opt": m_opt, "m_eq_optimalCPU": m_model,
+               "predicted_penalty_m1": cost(tpw, 1) / cost(tpw, m_opt)}
         for tag, m in (("opt", m_opt), ("m1", 1)):
             chunk = m * max(1, 50 // m)
-            nchunks = max(1, math.ceil(args.t2e_seconds / ((t_G + t_A / m) * chunk)))
+            nchunks = max(1, math.ceil(args.t2e_seconds / (steps[m] / m * chunk)))
             acc.zero_()
             torch.cuda.synchronize()
             a, b = _events(torch)
@@ -622,10 +652,89 @@ def run_t2e(args):
         rows.append(res)
         print(json.dumps(res), flush=True)
         del pos, lp, sw, acc, series
-    print(json.dumps({"config": "time to error, E/N of liquid 4He, FP32, Gaussian moves, m from Eq. optimalCPU",
+    print(json.dumps({"config": "time to error, E/N of liquid 4He, FP32, Gaussian moves, energy on the GPU every m",
                       "t_sigma2_s_mK2_by_N": {str(r["N"]): r["opt"]["t_sigma2_s_mK2"] for r in rows},
                       "t_sigma2_per_atom_s_mK2": {str(r["N"]): r["opt"]["t_sigma2_s_mK2"] / r["N"] for r in rows}}),
           flush=True)
+    return 0
+
+
+def run_c3(args):
+    """The paper-sized statistics run: N = 1952 at 0.02186 A^-3, 528 walkers in FP32 (the bench
+    workload: cube step bisected to about 50 % acceptance), 200 equilibration + 5000 measured
+    sweeps, E_L every 5, 50 blocks of 100 sweeps averaged in FP64; beside it the same chains in FP64
+    on the first 152 walkers (one per SM), 200 + --c3-fp64-sweeps measured sweeps (the full FP64
+    run would take about half an hour).  E/N of both with their errors and the combined 2 sigma."""
+    import torch
+    import paper_1312_1282_gb300 as q
+    torch.cuda.set_device(0)
+    n, W = N_ATOMS, WALKERS
+    L = qi.box_side(n, qi.RHO_HE)
+    pad = qi.pad4(n)
+    seed = 0x5EED0003
+
+    def descs(step, walkers):
+        return q.descs([(n, pad, w * 3 * pad, w, L, 0.0, qi.B_HE, 5.0, step) for w in range(walkers)])
+
+    def state(prec, walkers):
+        dt = torch.float64 if prec == q.QMC_FP64 else torch.float32
+        return (torch.empty(walkers * 3 * pad, dtype=dt, device="cuda"),
+                torch.zeros(walkers, dtype=torch.float64, device="cuda"),
+                torch.zeros(walkers, dtype=torch.int64, device="cuda"),
+                torch.zeros(walkers, 8, dtype=torch.float64, device="cuda"))
+
+    opt = q.options(precision=q.QMC_FP32, recompute_every=50)
+    pos, lp, sw, acc = state(q.QMC_FP32, W)
+    q.qmc_init_walkers(descs(0.8, W), seed, 0.1, opt, pos)
+    q.qmc_log_psi(descs(0.8, W), opt, pos, lp)
+    lo, hi, step = 0.1, 3.0, 0.8
+    for _ in range(5):  # step bisection on 4-sweep probes of the chains (as in the headline run)
+        acc.zero_()
+        q.qmc_sweep(descs(step, W), opt, pos, lp, sw, seed, 4, 0, acc)
+        rate = acc[:, 7].sum().item() / (W * n * 4)
+        lo, hi = (step, hi) if rate > 0.5 else (lo, step)
+        step = 0.5 * (lo + hi)
+    d = descs(step, W)
+    q.qmc_autotune(d, opt, pos)
+    t0 = time.time()
+    q.qmc_sweep(d, opt, pos, lp, sw, seed, 200, 0, acc)
+    blocks = []
+    walker_sum = torch.zeros(W, dtype=torch.float64, device="cuda")
+    for _ in range(50):
+        acc.zero_()
+        q.qmc_sweep(d, opt, pos, lp, sw, seed, 100, 5, acc)
+        e = acc[:, 0] / acc[:, 6] / n
+        walker_sum += e
+        blocks.append(float(e.mean()))
+    torch.cuda.synchronize()
+    t32 = time.time() - t0
+    assert q.qmc_status(None, 600000) == 0
+    b = np.array(blocks)
+    wm = (walker_sum / 50).cpu().numpy()
+    fp32 = {"E": float(b.mean()), "err_blocks": float(b.std(ddof=1) / math.sqrt(len(b))),
+            "err_walkers": float(wm.std(ddof=1) / math.sqrt(W)), "walkers": W, "sweeps": 5000, "seconds": t32}
+
+    W64 = min(W, torch.cuda.get_device_properties(0).multi_processor_count)
+    opt64 = q.options(precision=q.QMC_FP64, recompute_every=50)
+    pos64, lp64, sw64, acc64 = state(q.QMC_FP64, W64)
+    d64 = descs(step, W64)
+    q.qmc_init_walkers(d64, seed, 0.1, opt64, pos64)
+    q.qmc_log_psi(d64, opt64, pos64, lp64)
+    t0 = time.time()
+    q.qmc_sweep(d64, opt64, pos64, lp64, sw64, seed, 200, 0, acc64)
+    acc64.zero_()
+    q.qmc_sweep(d64, opt64, pos64, lp64, sw64, seed, args.c3_fp64_sweeps, 5, acc64)
+    torch.cuda.synchronize()
+    t64 = time.time() - t0
+    assert q.qmc_status(None, 600000) == 0
+    e64 = (acc64[:, 0] / acc64[:, 6] / n).cpu().numpy()
+    fp64 = {"E": float(e64.mean()), "err_walkers": float(e64.std(ddof=1) / math.sqrt(W64)), "walkers": W64,
+            "sweeps": args.c3_fp64_sweeps, "seconds": t64}
+    err32 = max(fp32["err_blocks"], fp32["err_walkers"])
+    res = {"config": "N=1952, 528 walkers FP32: 200 + 5000 sweeps, E_L every 5, 50 blocks; FP64 on 152 walkers",
+           "step_A": step, "fp32": fp32, "fp64": fp64, "diff_mK": 1e3 * (fp32["E"] - fp64["E"]),
+           "combined_2sigma_mK": 2e3 * math.hypot(err32, fp64["err_walkers"])}
+    print(json.dumps(res), flush=True)
     return 0
 
 
@@ -648,10 +757,11 @@ def main():
     ap.add_argument("--equil", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--large-n", type=int, default=10000, help="large: atoms per walker")
+    ap.add_argument("--c3-fp64-sweeps", type=int, default=600, help="c3: measured FP64 sweeps")
     ap.add_argument("--large-sweeps", type=int, default=20, help="large: sweeps per step")
     ap.add_argument("--t2e-seconds", type=float, default=3.0, help="t2e: production seconds per N and m")
     ap.add_argument("--t2e-sizes", default="", help="t2e: comma-separated N (default 128..4000)")
-    ap.add_argument("--config", default="headline", choices=["headline", "uneven", "large", "fp64cmp", "t2e"],
+    ap.add_argument("--config", default="headline", choices=["headline", "uneven", "large", "fp64cmp", "t2e", "c3"],
                     help="headline: the benchmark line; the others measure the other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -666,6 +776,8 @@ def main():
         return run_fp64cmp(args)
     if args.config == "t2e":
         return run_t2e(args)
+    if args.config == "c3":
+        return run_c3(args)
     return run_native(args)
 
 

@@ -268,12 +268,13 @@ struct Packed5 {
         hL2 = make_float2(J.hL2, J.hL2);
         m1 = make_float2(-1.f, -1.f);
     }
-    // |d| folded to the nearest image: min(|d|, L - |d|), for two differences at once
+    // |d| folded to the nearest image: min(|d|, L - |d|), for two differences at once (scalar
+    // subtractions, which take |d| as an operand modifier, measured faster than one packed FFMA2
+    // on explicit absolute values)
     __device__ __forceinline__ float2 fold(float2 d) const
     {
-        const float2 a = make_float2(fabsf(d.x), fabsf(d.y));
-        const float2 b = __ffma2_rn(a, m1, L);
-        return make_float2(fminf(a.x, b.x), fminf(a.y, b.y));
+        const float ax = fabsf(d.x), ay = fabsf(d.y);
+        return make_float2(fminf(ax, L.x - ax), fminf(ay, L.y - ay));
     }
     // acc += q^5 + w^5 of two partners, i.e. (u(r) + K) / c: the constant and the factor c are
     // applied once per partner sum, and the last power of each term is fused into the add
