@@ -118,14 +118,17 @@ struct SweepArgs {
     int *q_prog;             // [W] chunks done (bit 30: walker faulted, its chunks are skipped)
 };
 
-// Moves per batch of the sweep: the partner loop serves KB trial moves at once and the group
-// reduces their KB sums with one barrier (see move_batch).  Measured on GB300 at N = 1952,
-// 528 walkers, 128 threads per walker: KB = 1 is fastest (21.8 ms per 5 sweeps; KB = 2 22.3 ms,
-// KB = 4 31.7 ms, limited by registers), so it is the default; larger KB stays available.
+// Moves per batch of the FP32 sweep: the partner loop serves KB trial moves at once and the
+// group reduces their KB sums with one barrier (see move_batch); the FP64 sweep takes one move
+// at a time (its registers are twice as wide).  Measured on GB300 at N = 1952, 528 walkers,
+// 128 threads per walker, 5 sweeps without / with one energy sample: KB = 1 18.7 / 21.6 ms,
+// KB = 2 17.8 / 20.7 ms (the batch loop unrolled once; unrolled twice it spilled registers and
+// took 22.3 ms with the energy), so KB = 2 is the default.
 #ifndef QMC_KB
-#define QMC_KB 1
+#define QMC_KB 2
 #endif
 constexpr int KB = QMC_KB;
+template <typename T> constexpr int kb_of() { return std::is_same<T, float>::value ? KB : 1; }
 
 // Shared memory of one group, in this order: positions x | y | z (stride elements of T each),
 // reduction slots (2 phases of TPW/32 doubles, 2 phases of KB x TPW/32 T's), the cross terms of
@@ -725,7 +728,7 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
             acco[i] = make_float2(0.f, 0.f);
             accn[i] = make_float2(0.f, 0.f);
         }
-#pragma unroll 2
+#pragma unroll (K == 1 ? 2 : 1)
         for (int c = gtid; c < nv; c += TPW) {
             float4 X = reinterpret_cast<const float4 *>(sx)[c];
             float4 Y = reinterpret_cast<const float4 *>(sy)[c];
@@ -916,7 +919,7 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
 constexpr int PIPE_UNROLL = QMC_PIPE_UNROLL;
 template <typename T, int MEXP, bool SYM, int TPW> constexpr bool pipe_moves()
 {
-    return QMC_PIPE && std::is_same<T, float>::value && MEXP == 5 && SYM && KB == 1 && TPW >= 64;
+    return QMC_PIPE && std::is_same<T, float>::value && MEXP == 5 && SYM && kb_of<T>() == 1 && TPW >= 64;
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -1068,7 +1071,8 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
     const unsigned long long k0 = a.sweep[slot];
     double *A = a.accum + 8 * (size_t)slot;
     int nacc = 0;
-    Recent<T, KB> rec;
+    constexpr int K = kb_of<T>();  // moves per batch
+    Recent<T, K> rec;
     rec.clear();
     const int lane = gtid & 31;
     const uint32_t wid = d.wid;
@@ -1204,11 +1208,11 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
                 bool acc_p;  // the block's last move is decided before the next block
                 if (pend && !pipe_resolve(acc_p)) return false;
             } else {
-                for (; tt + KB <= cnt; tt += KB) {
-                    int bs[KB];
-                    T bdx[KB], bdy[KB], bdz[KB], bxi[KB];
+                for (; tt + K <= cnt; tt += K) {
+                    int bs[K];
+                    T bdx[K], bdy[K], bdz[K], bxi[K];
 #pragma unroll
-                    for (int i = 0; i < KB; ++i) {
+                    for (int i = 0; i < K; ++i) {
                         bs[i] = __shfl_sync(FULL, my_s, tt + i);
                         bdx[i] = __shfl_sync(FULL, mdx, tt + i);
                         bdy[i] = __shfl_sync(FULL, mdy, tt + i);
@@ -1217,18 +1221,18 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
                     }
                     bool distinct = true;
 #pragma unroll
-                    for (int i = 0; i < KB; ++i)
+                    for (int i = 0; i < K; ++i)
 #pragma unroll
-                        for (int q = i + 1; q < KB; ++q) distinct &= bs[i] != bs[q];
+                        for (int q = i + 1; q < K; ++q) distinct &= bs[i] != bs[q];
                     bool ok = true;
                     if (distinct) {
-                        ok = move_batch<T, MEXP, SYM, TPW, KB, KB, GM>(J, sx, sy, sz, n, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
+                        ok = move_batch<T, MEXP, SYM, TPW, K, K, GM>(J, sx, sy, sz, n, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
                                                                    nacc, redT, dsm, phT, bar_id, gtid);
                     } else {
-                        for (int i = 0; i < KB && ok; ++i) {
+                        for (int i = 0; i < K && ok; ++i) {
                             const int s1[1] = {bs[i]};
                             const T x1[1] = {bdx[i]}, y1[1] = {bdy[i]}, z1[1] = {bdz[i]}, c1[1] = {bxi[i]};
-                            ok = move_batch<T, MEXP, SYM, TPW, 1, KB, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp,
+                            ok = move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp,
                                                                       nacc, redT, dsm, phT, bar_id, gtid);
                         }
                     }
@@ -1241,7 +1245,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
                     const int s1[1] = {__shfl_sync(FULL, my_s, tt)};
                     const T x1[1] = {__shfl_sync(FULL, mdx, tt)}, y1[1] = {__shfl_sync(FULL, mdy, tt)},
                             z1[1] = {__shfl_sync(FULL, mdz, tt)}, c1[1] = {__shfl_sync(FULL, mxi, tt)};
-                    if (!move_batch<T, MEXP, SYM, TPW, 1, KB, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
+                    if (!move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
                                                               dsm, phT, bar_id, gtid)) {
                         if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
                         return false;
