@@ -140,9 +140,10 @@ def _cpu_info():
 # ---------------------------------------------------------------------------------------------
 # the oracle on the host cores (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------------------------
-def oracle_sample(walkers: int, nsweeps: int, step: float, seed: int = 0x5EED0003):
+def oracle_sample(walkers: int, nsweeps: int, step: float, seed: int = 0x5EED0003, threads: int = 0):
     """Run the FP64 oracle on `walkers` walkers of the workload for nsweeps sweeps (local energy
-    after the last) with OpenMP over walkers.  Returns (pair evals, seconds, threads)."""
+    after the last) with OpenMP over walkers (`threads` of them, 0: all).  Returns (pair evals,
+    seconds, threads, sums)."""
     import oracle
     n = N_ATOMS
     L = qi.box_side(n, qi.RHO_HE)
@@ -150,7 +151,8 @@ def oracle_sample(walkers: int, nsweeps: int, step: float, seed: int = 0x5EED000
           for w in range(walkers)]
     pos = [oracle.init_walker(n, L, seed, w, 0.1) for w in range(walkers)]
     t0 = time.perf_counter()
-    _, _, _, acc, used = oracle.run_batch(ws, pos, [0.0] * walkers, [0] * walkers, nsweeps, nsweeps)
+    _, _, _, acc, used = oracle.run_batch(ws, pos, [0.0] * walkers, [0] * walkers, nsweeps, nsweeps,
+                                          nthreads=threads)
     dt = time.perf_counter() - t0
     return pair_evals_per_sweep(n) * nsweeps * walkers, dt, used, acc
 
@@ -340,8 +342,11 @@ def run_native(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cores, model = _cpu_info()
         pe, dt, used, _ = oracle_sample(cores, 1, step)
+        pe1, dt1, _, _ = oracle_sample(1, 1, step, threads=1)
         cpu = {"value": pe / dt, "unit": "pair evals/s", "cores": used, "kind": "oracle",
-               "sample": f"{cores} walkers x 1 sweep (+1 local energy) at N={N_ATOMS}, FP64 oracle, {model}"}
+               "sample": f"{cores} walkers x 1 sweep (+1 local energy) at N={N_ATOMS}, FP64 oracle, {model}",
+               "one_core": {"value": pe1 / dt1, "unit": "pair evals/s", "cores": 1,
+                            "sample": f"1 walker x 1 sweep (+1 local energy) at N={N_ATOMS}, one thread"}}
 
     if rank == 0:
         line = {

@@ -119,8 +119,9 @@ struct SweepArgs {
 };
 
 // Moves per batch of the FP32 sweep: the partner loop serves KB trial moves at once and the
-// group reduces their KB sums with one barrier (see move_batch); the FP64 sweep takes one move
-// at a time (its registers are twice as wide).  Measured on GB300 at N = 1952, 528 walkers,
+// group reduces their KB sums with one barrier (see move_batch); the FP64 sweep (registers twice
+// as wide) and groups of one warp (no barrier to save; measured slower with KB = 2 at N = 128)
+// take one move at a time.  Measured on GB300 at N = 1952, 528 walkers,
 // 128 threads per walker, 5 sweeps without / with one energy sample: KB = 1 18.7 / 21.6 ms,
 // KB = 2 17.8 / 20.7 ms (the batch loop unrolled once; unrolled twice it spilled registers and
 // took 22.3 ms with the energy), so KB = 2 is the default.
@@ -128,7 +129,7 @@ struct SweepArgs {
 #define QMC_KB 2
 #endif
 constexpr int KB = QMC_KB;
-template <typename T> constexpr int kb_of() { return std::is_same<T, float>::value ? KB : 1; }
+template <typename T, int TPW> constexpr int kb_of() { return std::is_same<T, float>::value && TPW >= 64 ? KB : 1; }
 
 // Shared memory of one group, in this order: positions x | y | z (stride elements of T each),
 // reduction slots (2 phases of TPW/32 doubles, 2 phases of KB x TPW/32 T's), the cross terms of
@@ -667,16 +668,28 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
 // Delta_i = S_i + sum_{k < i, accepted} D_ik is Eq. (JastrowUpdate) for the true configuration.
 // A batch that draws the same atom twice is done one move at a time.
 // ----------------------------------------------------------------------------------------------
-template <typename T, int KM> struct Recent {  // accepted moves of the previous batch (register copy)
+// Accepted moves of the previous batch (register copy): entry q holds move q of the batch, or
+// s[q] = -1.  Entries are only addressed by compile-time indices, so they stay in registers.
+template <typename T, int KM> struct Recent {
     int s[KM];
     T x[KM], y[KM], z[KM];
-    int cnt;
-    __device__ __forceinline__ void clear() { cnt = 0; }
+    __device__ __forceinline__ void clear()
+    {
+#pragma unroll
+        for (int q = 0; q < KM; ++q) s[q] = -1;
+    }
+    __device__ __forceinline__ void set(int q, int a, T px, T py, T pz)
+    {
+        s[q] = a;
+        x[q] = px;
+        y[q] = py;
+        z[q] = pz;
+    }
     __device__ __forceinline__ void lookup(int a, T &px, T &py, T &pz) const
     {
 #pragma unroll
         for (int q = 0; q < KM; ++q)
-            if (q < cnt && s[q] == a) {
+            if (s[q] == a) {
                 px = x[q];
                 py = y[q];
                 pz = z[q];
@@ -886,11 +899,7 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
                 sy[s[i]] = by[i];
                 sz[s[i]] = bz[i];
             }
-            rec.s[rec.cnt] = s[i];
-            rec.x[rec.cnt] = bx[i];
-            rec.y[rec.cnt] = by[i];
-            rec.z[rec.cnt] = bz[i];
-            ++rec.cnt;
+            rec.set(i, s[i], bx[i], by[i], bz[i]);
         }
     if (TPW == 32) __syncwarp();
     return true;
@@ -919,7 +928,7 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
 constexpr int PIPE_UNROLL = QMC_PIPE_UNROLL;
 template <typename T, int MEXP, bool SYM, int TPW> constexpr bool pipe_moves()
 {
-    return QMC_PIPE && std::is_same<T, float>::value && MEXP == 5 && SYM && kb_of<T>() == 1 && TPW >= 64;
+    return QMC_PIPE && std::is_same<T, float>::value && MEXP == 5 && SYM && kb_of<T, TPW>() == 1 && TPW >= 64;
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -1071,7 +1080,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
     const unsigned long long k0 = a.sweep[slot];
     double *A = a.accum + 8 * (size_t)slot;
     int nacc = 0;
-    constexpr int K = kb_of<T>();  // moves per batch
+    constexpr int K = kb_of<T, TPW>();  // moves per batch
     Recent<T, K> rec;
     rec.clear();
     const int lane = gtid & 31;
@@ -1107,11 +1116,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
                 sy[ps] = pby;
                 sz[ps] = pbz;
             }
-            rec.s[0] = ps;
-            rec.x[0] = pbx;
-            rec.y[0] = pby;
-            rec.z[0] = pbz;
-            rec.cnt = 1;
+            rec.set(0, ps, pbx, pby, pbz);
         }
         return true;
     };
