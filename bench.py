@@ -234,7 +234,11 @@ def run_native(args):
             hi = step
         step = 0.5 * (lo + hi)
     d = batch_descs(step)
-    tpw = q.qmc_autotune(d, opt, pos)
+    if args.tpw:  # a fixed launch shape (profiling runs), else the autotuner's choice
+        tpw = args.tpw
+        opt = q.options(precision=q.QMC_FP32, recompute_every=50, threads_per_walker=tpw)
+    else:
+        tpw = q.qmc_autotune(d, opt, pos)
     q.qmc_sweep(d, opt, pos, logpsi, sweeps, seed, args.equil, 0, accum)
     accum.zero_()
     torch.cuda.synchronize()
@@ -417,7 +421,11 @@ def run_uneven(args):
     acc = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
     q.qmc_init_walkers(d, 0x5EED0004, 0.1, opt, pos)
     q.qmc_log_psi(d, opt, pos, lp)
-    tpw = q.qmc_autotune(d, opt, pos)
+    if args.tpw:
+        tpw = args.tpw
+        opt = q.options(precision=q.QMC_FP32, recompute_every=50, threads_per_walker=tpw)
+    else:
+        tpw = q.qmc_autotune(d, opt, pos)
     q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0004, args.equil, 0, acc)
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()
@@ -761,6 +769,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--equil", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--tpw", type=int, default=0, help="threads per walker of the headline run (0: autotune)")
     ap.add_argument("--large-n", type=int, default=10000, help="large: atoms per walker")
     ap.add_argument("--c3-fp64-sweeps", type=int, default=600, help="c3: measured FP64 sweeps")
     ap.add_argument("--large-sweeps", type=int, default=20, help="large: sweeps per step")

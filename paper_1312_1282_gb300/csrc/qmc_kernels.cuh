@@ -668,28 +668,28 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
 // Delta_i = S_i + sum_{k < i, accepted} D_ik is Eq. (JastrowUpdate) for the true configuration.
 // A batch that draws the same atom twice is done one move at a time.
 // ----------------------------------------------------------------------------------------------
-// Accepted moves of the previous batch (register copy): entry q holds move q of the batch, or
-// s[q] = -1.  Entries are only addressed by compile-time indices, so they stay in registers.
+// Accepted moves of the previous batch (a private copy per thread), appended in batch order.
+// With two or more moves per batch the entries are addressed by the running count, so the
+// compiler keeps them in local memory (L1): measured faster at N = 1952, 128 threads per walker
+// (20.9 against 21.7 ms per step) than entries held in registers across the partner loop.
 template <typename T, int KM> struct Recent {
     int s[KM];
     T x[KM], y[KM], z[KM];
-    __device__ __forceinline__ void clear()
+    int cnt;
+    __device__ __forceinline__ void clear() { cnt = 0; }
+    __device__ __forceinline__ void add(int a, T px, T py, T pz)
     {
-#pragma unroll
-        for (int q = 0; q < KM; ++q) s[q] = -1;
-    }
-    __device__ __forceinline__ void set(int q, int a, T px, T py, T pz)
-    {
-        s[q] = a;
-        x[q] = px;
-        y[q] = py;
-        z[q] = pz;
+        s[cnt] = a;
+        x[cnt] = px;
+        y[cnt] = py;
+        z[cnt] = pz;
+        ++cnt;
     }
     __device__ __forceinline__ void lookup(int a, T &px, T &py, T &pz) const
     {
 #pragma unroll
         for (int q = 0; q < KM; ++q)
-            if (s[q] == a) {
+            if (q < cnt && s[q] == a) {
                 px = x[q];
                 py = y[q];
                 pz = z[q];
@@ -899,7 +899,7 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
                 sy[s[i]] = by[i];
                 sz[s[i]] = bz[i];
             }
-            rec.set(i, s[i], bx[i], by[i], bz[i]);
+            rec.add(s[i], bx[i], by[i], bz[i]);
         }
     if (TPW == 32) __syncwarp();
     return true;
@@ -1116,7 +1116,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
                 sy[ps] = pby;
                 sz[ps] = pbz;
             }
-            rec.set(0, ps, pbx, pby, pbz);
+            rec.add(ps, pbx, pby, pbz);
         }
         return true;
     };
