@@ -54,6 +54,8 @@ int cuda_fail(cudaError_t e, const char *what)
 struct DeviceState {
     unsigned *err = nullptr;
     int nsm = 0;
+    float *fscr = nullptr;  // drift arrays of the tiled energy pass kept in global memory
+    size_t fscr_bytes = 0;
 };
 
 std::mutex g_mu;
@@ -157,6 +159,34 @@ bool use_gmem(int precision, int maxpad, int tpw)
 bool use_tile(int precision, int maxpad, int tpw, int G)
 {
     return precision == QMC_FP32 && (size_t)G * smem_group(precision, maxpad, tpw, true) <= MAX_SMEM;
+}
+
+// CTAs of G groups that fit one SM by shared memory (228 KB, 1 KB reserved per CTA) and by
+// registers (the sweep kernels' launch bounds give at most 128 registers a thread for groups of
+// up to 256 threads, 512 resident threads; larger groups run one CTA)
+int ctas_per_sm(size_t smem_cta, int tpw, int G)
+{
+    const int by_regs = tpw <= 256 ? std::max(1, 512 / (G * tpw)) : 1;
+    const int by_smem = (int)(233472 / (smem_cta + 1024));
+    return std::min(by_regs, by_smem);
+}
+
+// Sweep energy pass: 1 = tiled with the drift arrays in shared memory, 2 = tiled with them in
+// global scratch (when the arrays in shared memory would leave fewer walkers resident per SM,
+// e.g. N > 2400 with 128 threads per walker), 0 = by rows.  QMC_TILE_GLOBAL=1 in the
+// environment makes every tiled sweep use global scratch (used by the tests).
+int sweep_tile_mode(int precision, int maxpad, int tpw, int G)
+{
+    static const bool forced = [] {
+        const char *e = std::getenv("QMC_TILE_GLOBAL");
+        return e && e[0] == '1';
+    }();
+    if (precision != QMC_FP32) return 0;
+    const size_t plain = smem_group(precision, maxpad, tpw, false), tiled = smem_group(precision, maxpad, tpw, true);
+    if (forced) return 2;
+    if ((size_t)G * tiled <= MAX_SMEM && ctas_per_sm((size_t)G * tiled, tpw, G) >= ctas_per_sm((size_t)G * plain, tpw, G))
+        return 1;
+    return 2;
 }
 
 int sites_of(int n)
@@ -331,13 +361,18 @@ struct Shape {
     int stride, tile, gmem;
     size_t smem;  // per group
 };
-Shape shape_of(const Plan &P, int precision, int tpw, int G, bool energy_pass)
+Shape shape_of(const Plan &P, int precision, int tpw, int G, bool energy_pass, bool sweep = false)
 {
     Shape sh;
     sh.gmem = use_gmem(precision, P.maxpad, tpw) ? 1 : 0;
     sh.stride = sh.gmem ? 0 : stride_of(P.maxpad);
-    sh.tile = (!sh.gmem && energy_pass && use_tile(precision, P.maxpad, tpw, G)) ? 1 : 0;
-    sh.smem = sh.gmem ? smem_group(precision, 0, tpw, false) : smem_group(precision, P.maxpad, tpw, sh.tile != 0);
+    if (sh.gmem || !energy_pass)
+        sh.tile = 0;
+    else if (sweep)
+        sh.tile = sweep_tile_mode(precision, P.maxpad, tpw, G);
+    else
+        sh.tile = use_tile(precision, P.maxpad, tpw, G) ? 1 : 0;
+    sh.smem = sh.gmem ? smem_group(precision, 0, tpw, false) : smem_group(precision, P.maxpad, tpw, sh.tile == 1);
     return sh;
 }
 
@@ -400,7 +435,7 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     const int tpw = tpw_force ? tpw_force : choose_tpw(P, o, p.dev, p.ds->nsm);
     if (nsweeps == 0) return QMC_OK;
     const int G = choose_groups(P, o->precision, tpw, p.ds->nsm);
-    const Shape sh = shape_of(P, o->precision, tpw, G, true);
+    const Shape sh = shape_of(P, o->precision, tpw, G, true, true);
     SweepArgs a;
     a.walkers = P.d_walkers;
     a.order = P.d_order;
@@ -468,6 +503,20 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
             if (e != cudaSuccess) return cuda_fail(e, "walker queue init");
             g_launches.fetch_add(1);
         }
+    }
+    a.fscr = nullptr;
+    if (a.tile == 2) {  // drift scratch of every resident group, grown on demand (not under capture)
+        const size_t need = (size_t)grid * G * 3 * sh.stride * sizeof(float);
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (p.ds->fscr_bytes < need) {
+            if (p.ds->fscr) cudaFree(p.ds->fscr);
+            p.ds->fscr = nullptr;
+            p.ds->fscr_bytes = 0;
+            e = cudaMalloc(&p.ds->fscr, need);
+            if (e != cudaSuccess) return cuda_fail(e, "drift scratch");
+            p.ds->fscr_bytes = need;
+        }
+        a.fscr = p.ds->fscr;
     }
     e = launch_sweep(o->precision, tpw, v, grid, G * tpw, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
@@ -709,7 +758,10 @@ void qmc_shutdown(void)
     g_tuned.clear();
     for (auto &ds : g_dev) {
         if (ds.err) cudaFree(ds.err);
+        if (ds.fscr) cudaFree(ds.fscr);
         ds.err = nullptr;
+        ds.fscr = nullptr;
+        ds.fscr_bytes = 0;
         ds.nsm = 0;
     }
 }
@@ -845,7 +897,8 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     a.W = W;
     a.G = G;
     a.stride = sh.stride;
-    a.tile = sh.tile;
+    a.tile = sh.tile;  // 0 or 1: no drift scratch to allocate
+    a.fscr = nullptr;
     a.gmem = sh.gmem;
     a.pos = pos;
     a.logpsi = logpsi;

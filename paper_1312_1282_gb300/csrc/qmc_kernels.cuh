@@ -98,7 +98,8 @@ struct SweepArgs {
     int W;
     int G;                     // walkers per CTA
     int stride;                // shared-memory block stride (elements): largest pad, rounded up to 32
-    int tile;                  // 1: local energy by the tiled pass (needs the drift arrays in smem)
+    int tile;                  // local energy by the tiled pass: 1 drift arrays in smem, 2 in fscr
+    float *fscr;               // tile 2: 3 x stride floats of drift per resident group (L2-resident)
     int gmem;                  // 1: walkers too large for shared memory stay in HBM (updated in place)
     void *pos;
     double *logpsi;
@@ -176,6 +177,13 @@ template <typename T> struct GroupMem {
         fx = reinterpret_cast<float *>(base + g.F);
         fy = fx + stride;
         fz = fy + stride;
+    }
+    // drift arrays of the tiled energy pass in a group's own block of global scratch
+    __device__ __forceinline__ void use_global_drift(float *f, int stride)
+    {
+        fx = f;
+        fy = f + stride;
+        fz = f + 2 * (size_t)stride;
     }
     // positions of a walker too large for shared memory: its own blocks in HBM, used in place
     __device__ __forceinline__ void use_global(T *gx, int pad)
@@ -1356,7 +1364,8 @@ __global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_ker
     const int item = blockIdx.x * a.G + g;
     if (!a.dynamic && item >= a.W) return;  // only group barriers follow, so whole groups may leave
     GroupMem<T> mem;
-    mem.bind(smem + (size_t)g * group_smem<T>(a.stride, TPW, a.tile), a.stride, TPW, a.tile);
+    mem.bind(smem + (size_t)g * group_smem<T>(a.stride, TPW, a.tile == 1), a.stride, TPW, a.tile == 1);
+    if (a.tile == 2) mem.use_global_drift(a.fscr + (size_t)3 * a.stride * (blockIdx.x * a.G + g), a.stride);
     unsigned jm = 0;  // pipelined moves arrived on the group's mbarriers
     if constexpr (pipe_moves<T, MEXP, SYM, TPW>()) {
         if (gtid == 0) {
