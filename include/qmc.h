@@ -115,6 +115,11 @@ int qmc_init_walkers(const qmc_walker_desc *d, int W, uint64_t seed, double jitt
  *            sum T_F, number of samples, number of accepted moves}
  * The same (seed, id, k) always reproduces the same chain: a run split over several calls is
  * bit-identical to one call.
+ * Device memory: the first call of a batch allocates its walker table (and, for batches of
+ * more walkers than SMs, the walker queue); an FP32 call with an energy sample whose drift
+ * arrays would crowd shared memory (about N > 2400 at 128 threads per walker) also grows a
+ * library-owned drift scratch.  Under CUDA stream capture no allocation is possible, so a
+ * captured call must follow an uncaptured call of the same batch shape.
  */
 int qmc_sweep(const qmc_walker_desc *d, int W, const qmc_options *opt, void *pos, double *logpsi,
               uint64_t *sweep, uint64_t seed, int nsweeps, int energy_every, double *accum,
