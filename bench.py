@@ -321,6 +321,18 @@ def run_native(args):
     e2e_ms = x0.elapsed_time(x1) / e2e_steps
     h2d = host_pos.numel() * 4 + W * 8 * 10
     d2h = out_pos.numel() * 4 + W * 8 * 8
+    # the copies alone, for the breakdown of the end-to-end step
+    x0.record(stream)
+    for _ in range(e2e_steps):
+        pos.copy_(host_pos, non_blocking=True)
+        logpsi.copy_(host_lp, non_blocking=True)
+        sweeps.copy_(host_sw, non_blocking=True)
+        accum.copy_(host_acc, non_blocking=True)
+        out_pos.copy_(pos, non_blocking=True)
+        out_acc.copy_(accum, non_blocking=True)
+    x1.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = x0.elapsed_time(x1) / e2e_steps
 
     # ---- roofline of the dominant kernel (the sweep kernel: one launch per step) ----
     peaks = _peaks()
@@ -369,7 +381,7 @@ def run_native(args):
             "fp64_plain": {"value": fp64_plain, "unit": "pair evals/s", "walkers": 1,
                            "speedup_fp32_batched": value / world / fp64_plain},
             "e2e": {"value": pe_step * world / (e2e_ms * 1e-3), "unit": "pair evals/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "copy_ms_per_step": copy_ms},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
                          "frac": achieved / peak_tops, "traffic": traffic,
