@@ -27,7 +27,7 @@ namespace {
 
 constexpr size_t MAX_SMEM = 232448;  // opt-in dynamic shared memory per CTA (227 KB)
 #ifndef QMC_CHUNK_DIV
-#define QMC_CHUNK_DIV 8  // persistent sweep: chunks of 1/QMC_CHUNK_DIV sweep of the largest walker
+#define QMC_CHUNK_DIV 8  // persistent sweep: chunks of 1/QMC_CHUNK_DIV sweep of the largest walker (>= 128 moves)
 #endif
 constexpr int MAX_DEVICES = 64;
 constexpr size_t MAX_PLANS = 32;
@@ -487,10 +487,13 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
             std::lock_guard<std::mutex> lk(occ_mu);
             occ_cache[okey] = ctas;
         }
-        const long long chunk = std::max(32, ((P.maxn + QMC_CHUNK_DIV - 1) / QMC_CHUNK_DIV + 31) / 32 * 32);
+        const long long chunk = std::max(128, ((P.maxn + QMC_CHUNK_DIV - 1) / QMC_CHUNK_DIV + 31) / 32 * 32);
         long long total = 0;
         for (int w = 0; w < W; ++w) total += ((long long)nsweeps * d[w].n + chunk - 1) / chunk;
-        if (ctas > 0 && total < (1ll << 31)) {
+        // a batch that fills every SM with the same number of resident groups gains nothing from
+        // the queue: each group keeps its walker for the whole call
+        const bool even = W % p.ds->nsm == 0 && (long long)W <= (long long)ctas * p.ds->nsm * G;
+        if (ctas > 0 && !even && total < (1ll << 31)) {
             a.dynamic = 1;
             a.chunk_moves = (int)chunk;
             a.q_total = (unsigned)total;
