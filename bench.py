@@ -307,20 +307,24 @@ def run_native(args):
     e2e_steps = max(3, min(args.steps, 10))
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def e2e_step():
+    # each step's sweep counters advance as in the timed loop (a fresh pinned tensor per step, so
+    # no host write races an asynchronous copy), so the periodic ln psi recompute keeps its rate
+    host_sws = [(host_sw + SWEEPS_PER_STEP * i).pin_memory() for i in range(e2e_steps + 1)]
+
+    def e2e_step(i):
         pos.copy_(host_pos, non_blocking=True)
         logpsi.copy_(host_lp, non_blocking=True)
-        sweeps.copy_(host_sw, non_blocking=True)
+        sweeps.copy_(host_sws[i], non_blocking=True)
         accum.copy_(host_acc, non_blocking=True)
         one_step()
         out_pos.copy_(pos, non_blocking=True)
         out_acc.copy_(accum, non_blocking=True)
 
-    e2e_step()  # untimed: first use of the pinned buffers
+    e2e_step(0)  # untimed: first use of the pinned buffers
     torch.cuda.synchronize()
     x0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
+    for i in range(e2e_steps):
+        e2e_step(i + 1)
     x1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = x0.elapsed_time(x1) / e2e_steps
@@ -331,7 +335,7 @@ def run_native(args):
     for _ in range(e2e_steps):
         pos.copy_(host_pos, non_blocking=True)
         logpsi.copy_(host_lp, non_blocking=True)
-        sweeps.copy_(host_sw, non_blocking=True)
+        sweeps.copy_(host_sws[0], non_blocking=True)
         accum.copy_(host_acc, non_blocking=True)
         out_pos.copy_(pos, non_blocking=True)
         out_acc.copy_(accum, non_blocking=True)
