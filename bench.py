@@ -773,11 +773,16 @@ def run_c3(args):
 
 
 def _kernel_hash():
+    """Hash of the sources that define the sweep kernel's device code (the traffic record of
+    profiles/sweep_traffic.json is used only while it matches)."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1312_1282_gb300", "csrc")
-    for nm in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, nm), "rb") as fh:
+    files = [os.path.join(csrc, nm) for nm in ("qmc_device.cuh", "qmc_kernels.cuh", "qmc_launch.h", "qmc_k_sweep.inc",
+                                               "qmc_k_sweep_f32_small.cu", "qmc_k_sweep_f32_big.cu")]
+    files.append(os.path.join(ROOT, "include", "qmc.h"))
+    for f in files:
+        with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
