@@ -206,6 +206,33 @@ def test_persistent_queue_mode_matches_oracle_and_static_path():
         np.testing.assert_allclose(acc[w, :6], oacc[:6], rtol=1e-10, atol=1e-9)
 
 
+def test_dominant_walker_takes_the_whole_call():
+    """An uneven batch in which one walker's pair work dominates: that walker runs its whole call
+    as one chunk of the persistent queue, the others in chunks.  Chains as the oracle's (FP64, bit
+    for bit) and as the one-walker-per-group path."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    ns = [600] + [64] * (nsm + 20)
+    W = len(ns)
+    A = lattice_batch(ns, q.QMC_FP64, seed=9)
+    B = lattice_batch(ns, q.QMC_FP64, seed=9)
+    opt = q.options(precision=q.QMC_FP64, recompute_every=2)
+    la, sa, aa = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lb, sb, ab = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    q.qmc_log_psi(A.d, opt, A.pos, la)
+    q.qmc_log_psi(B.d, opt, B.pos, lb)
+    q.qmc_sweep(A.d, opt, A.pos, la, sa, 0xB16, 3, 1, aa)
+    q.qmc_sweep_static(B.d, opt, B.pos, lb, sb, 0xB16, 3, 1, ab)
+    assert q.qmc_status(timeout_ms=120000) == 0
+    assert torch.equal(A.pos, B.pos) and torch.equal(sa, sb)
+    np.testing.assert_allclose(la.cpu().numpy(), lb.cpu().numpy(), rtol=1e-12)
+    np.testing.assert_allclose(aa.cpu().numpy(), ab.cpu().numpy(), rtol=1e-12)
+    acc = aa.cpu().numpy()
+    for w in (0, 1, W - 1):
+        pos, olp, ok, oacc, _ = _oracle_chain(A, w, 0xB16, 3, 1, opt)
+        assert np.array_equal(A.positions(w), pos)
+        assert acc[w, 7] == oacc[7] and acc[w, 6] == oacc[6]
+
+
 def test_persistent_queue_mode_survives_a_faulted_walker():
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     W = nsm + 5
