@@ -71,7 +71,7 @@ struct Plan {
     int *d_order = nullptr;
     uint2 *q_slots = nullptr;  // walker FIFO of the persistent sweep
     int *q_prog = nullptr;
-    unsigned *q_ctr = nullptr;  // head, tail
+    unsigned *q_ctr = nullptr;  // head, tail, next dominant walker (mixed sweep)
     int maxn = 0, maxpad = 0, maxsites = 0;
     bool m5 = true;
 };
@@ -297,7 +297,7 @@ int get_plan(const qmc_walker_desc *d, int W, const qmc_options *o, cudaStream_t
     if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int) * (size_t)W);
     if (e == cudaSuccess) e = cudaMalloc(&p->q_slots, sizeof(uint2) * (size_t)W);
     if (e == cudaSuccess) e = cudaMalloc(&p->q_prog, sizeof(int) * (size_t)W);
-    if (e == cudaSuccess) e = cudaMalloc(&p->q_ctr, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&p->q_ctr, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_walkers, host.data(), sizeof(DevWalker) * (size_t)W, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_order, order.data(), sizeof(int) * (size_t)W, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -342,6 +342,22 @@ int choose_tpw(const Plan &P, const qmc_options *o, int dev, int nsm)
     int t = pow2_at_least((int)std::ceil(512.0 * nsm / P.W));
     t = std::min(t, pow2_at_least(chunks));
     return std::max(32, std::min(t, 1024));
+}
+
+// the library-owned drift scratch of the tiled energy pass, at least `need` bytes (not under capture)
+int drift_scratch(DeviceState *ds, size_t need, float **out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (ds->fscr_bytes < need) {
+        if (ds->fscr) cudaFree(ds->fscr);
+        ds->fscr = nullptr;
+        ds->fscr_bytes = 0;
+        cudaError_t e = cudaMalloc(&ds->fscr, need);
+        if (e != cudaSuccess) return cuda_fail(e, "drift scratch");
+        ds->fscr_bytes = need;
+    }
+    *out = ds->fscr;
+    return QMC_OK;
 }
 
 // Walkers per CTA: one, unless the batch has so many small walkers that the 32-CTA-per-SM
@@ -418,6 +434,105 @@ int prepare(const qmc_walker_desc *d, int W, const qmc_options *o, cudaStream_t 
     if ((rc = current_device(p.dev))) return rc;
     if ((rc = device_state(p.dev, p.ds))) return rc;
     return get_plan(d, W, o, st, p.plan);
+}
+
+// Uneven batch with dominant walkers (n >= whole_n): the mixed kernel runs those on whole CTAs of
+// MIXED_TPWB threads, one whole call each, and the other walkers on groups of tpw threads from
+// the queue.  Returns -1 (nothing launched) when the batch does not suit it: FP32 exponent-5
+// symmetrised walkers in shared memory, tpw 64 or 128, both phases within one CTA's shared memory.
+// QMC_MIXED=0 in the environment turns it off.
+int mixed_sweep(const qmc_walker_desc *d, int W, const qmc_options *o, const Plan &P, Prep &p, int tpw, Variant v,
+                int whole_n, int nsweeps, const SweepArgs &a, cudaStream_t st)
+{
+    static const bool off = [] {
+        const char *e = std::getenv("QMC_MIXED");
+        return e && e[0] == '0';
+    }();
+    if (off || o->precision != QMC_FP32 || v != V5S || (tpw != 64 && tpw != 128)) return -1;
+    int n_big = 0, maxpad_b = 0, maxpad_s = 0, maxn_s = 0;
+    for (int w = 0; w < W; ++w) {
+        if (d[w].n >= whole_n) {
+            ++n_big;
+            maxpad_b = std::max(maxpad_b, (int)d[w].pad_n);
+        } else {
+            maxpad_s = std::max(maxpad_s, (int)d[w].pad_n);
+            maxn_s = std::max(maxn_s, (int)d[w].n);
+        }
+    }
+    if (n_big == 0 || n_big == W) return -1;
+    if (use_gmem(QMC_FP32, maxpad_b, MIXED_TPWB) || use_gmem(QMC_FP32, maxpad_s, tpw)) return -1;
+    const int Gs = MIXED_TPWB / tpw;
+    const int tile_b = sweep_tile_mode(QMC_FP32, maxpad_b, MIXED_TPWB, 1);
+    const int tile_s = sweep_tile_mode(QMC_FP32, maxpad_s, tpw, Gs);
+    const size_t smem_b = smem_group(QMC_FP32, maxpad_b, MIXED_TPWB, tile_b == 1);
+    const size_t smem_s = (size_t)Gs * smem_group(QMC_FP32, maxpad_s, tpw, tile_s == 1);
+    const size_t smem = std::max(smem_b, smem_s);
+    if (smem > MAX_SMEM) return -1;
+    static std::mutex mu;
+    static std::unordered_map<uint64_t, int> cache;
+    int key_v[3] = {p.dev, tpw, (int)smem};
+    const uint64_t key = fnv(key_v, sizeof key_v);
+    int ctas = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) ctas = it->second;
+    }
+    cudaError_t e;
+    if (ctas == 0) {
+        e = occupancy_sweep_mixed(tpw, smem, &ctas);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = ctas;
+    }
+    if (ctas < 1) return -1;
+    const int grid = ctas * p.ds->nsm;
+    const long long chunk = std::max(128, ((maxn_s + QMC_CHUNK_DIV - 1) / QMC_CHUNK_DIV + 31) / 32 * 32);
+    long long total = 0;
+    for (int w = 0; w < W; ++w)
+        if (d[w].n < whole_n) total += ((long long)nsweeps * d[w].n + chunk - 1) / chunk;
+    if (total >= (1ll << 31)) return -1;
+
+    SweepArgs big = a, small = a;
+    big.order = P.d_order;  // longest first: the dominant walkers lead the order
+    big.W = n_big;
+    big.G = 1;
+    big.stride = stride_of(maxpad_b);
+    big.tile = tile_b;
+    big.gmem = 0;
+    big.dynamic = 0;
+    small.order = P.d_order + n_big;
+    small.W = W - n_big;
+    small.G = Gs;
+    small.stride = stride_of(maxpad_s);
+    small.tile = tile_s;
+    small.gmem = 0;
+    small.dynamic = 1;
+    small.chunk_moves = (int)chunk;
+    small.whole_n = INT_MAX;
+    small.q_total = (unsigned)total;
+    small.q_head = P.q_ctr;
+    small.q_tail = P.q_ctr + 1;
+    small.q_slots = P.q_slots;
+    small.q_prog = P.q_prog;
+    big.fscr = small.fscr = nullptr;
+    const size_t fb = tile_b == 2 ? (size_t)grid * 3 * big.stride : 0;
+    const size_t fs = tile_s == 2 ? (size_t)grid * Gs * 3 * small.stride : 0;
+    if (fb + fs > 0) {
+        float *f = nullptr;
+        int rc = drift_scratch(p.ds, (fb + fs) * sizeof(float), &f);
+        if (rc) return rc;
+        if (fb) big.fscr = f;
+        if (fs) small.fscr = f + fb;
+    }
+    e = launch_queue_init(small.order, small.W, P.q_slots, P.q_prog, P.q_ctr, P.q_ctr + 1, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.q_ctr + 2, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(e, "walker queue init");
+    g_launches.fetch_add(1);
+    e = launch_sweep_mixed(tpw, grid, smem, st, small, big, P.q_ctr + 2);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed sweep launch");
+    g_launches.fetch_add(1);
+    return QMC_OK;
 }
 
 int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos, double *logpsi, uint64_t *sweep,
@@ -506,6 +621,10 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
             const long long tw = (long long)nsweeps * d[w].n;
             total += d[w].n >= whole_n ? 1 : (tw + chunk - 1) / chunk;
         }
+        if (whole_n < INT_MAX && ctas > 0) {
+            const int mrc = mixed_sweep(d, W, o, P, p, tpw, v, whole_n, nsweeps, a, st);
+            if (mrc != -1) return mrc;  // launched (or failed); -1: the batch does not suit it
+        }
         // a batch that fills every SM with the same number of resident groups gains nothing from
         // the queue: each group keeps its walker for the whole call
         const bool even = W % p.ds->nsm == 0 && (long long)W <= (long long)ctas * p.ds->nsm * G;
@@ -526,17 +645,7 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     }
     a.fscr = nullptr;
     if (a.tile == 2) {  // drift scratch of every resident group, grown on demand (not under capture)
-        const size_t need = (size_t)grid * G * 3 * sh.stride * sizeof(float);
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (p.ds->fscr_bytes < need) {
-            if (p.ds->fscr) cudaFree(p.ds->fscr);
-            p.ds->fscr = nullptr;
-            p.ds->fscr_bytes = 0;
-            e = cudaMalloc(&p.ds->fscr, need);
-            if (e != cudaSuccess) return cuda_fail(e, "drift scratch");
-            p.ds->fscr_bytes = need;
-        }
-        a.fscr = p.ds->fscr;
+        if ((rc = drift_scratch(p.ds, (size_t)grid * G * 3 * sh.stride * sizeof(float), &a.fscr))) return rc;
     }
     e = launch_sweep(o->precision, tpw, v, grid, G * tpw, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");

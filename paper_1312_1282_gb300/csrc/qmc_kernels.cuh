@@ -1350,6 +1350,39 @@ __device__ __forceinline__ void queue_push(const SweepArgs &a, int w)
 
 
 
+// Persistent mode: take ready walkers from the FIFO, advance each by one chunk, put it back.
+template <typename T, int MEXP, bool SYM, int TPW>
+__device__ void persistent_loop(const SweepArgs &a, GroupMem<T> &mem, int g, int gtid, unsigned &jm)
+{
+    constexpr int DEAD = 1 << 30;
+    for (;;) {
+        if (gtid == 0) *mem.bc = queue_pop(a, a.q_total);
+        group_sync<TPW>(1 + g);
+        const int w = *mem.bc;
+        group_sync<TPW>(1 + g);
+        if (w < 0) return;
+        // the walker was last written by another SM: acquire its state (positions, ln psi, sums)
+        cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
+        const DevWalker d = a.walkers[w];
+        const long long total = (long long)a.nsweeps * d.n;
+        const int c = a.q_prog[w];
+        const long long chunk = d.n >= a.whole_n ? total : (long long)a.chunk_moves;
+        const long long m0 = (long long)(c & (DEAD - 1)) * chunk;
+        const long long m1 = min(total, m0 + chunk);
+        bool ok = true;
+        if (!(c & DEAD))
+            ok = a.gmem ? run_range<T, MEXP, SYM, TPW, true>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total, jm)
+                        : run_range<T, MEXP, SYM, TPW, false>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total, jm);
+        __threadfence();  // this thread's stores of the walker state, before it is handed on
+        group_sync<TPW>(1 + g);
+        if (gtid == 0) {
+            a.q_prog[w] = (c + 1) | (ok ? 0 : DEAD);
+            __threadfence();
+            if (m1 < total) queue_push(a, w);
+        }
+    }
+}
+
 // CTAs hold up to 256 threads (TPW <= 256) or exactly one group; at least 1024 resident threads
 // per SM, i.e. at most 64 registers per thread.
 // Up to 128 registers per thread (at least 512 resident threads per SM) except for groups of
@@ -1384,34 +1417,46 @@ __global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_ker
             run_range<T, MEXP, SYM, TPW, false>(a, d, mem, gtid, 1 + g, 0, total, true, jm);
         return;
     }
-    // persistent: take ready walkers from the FIFO, advance each by one chunk, put it back
-    constexpr int DEAD = 1 << 30;
-    for (;;) {
-        if (gtid == 0) *mem.bc = queue_pop(a, a.q_total);
-        group_sync<TPW>(1 + g);
-        const int w = *mem.bc;
-        group_sync<TPW>(1 + g);
-        if (w < 0) return;
-        // the walker was last written by another SM: acquire its state (positions, ln psi, sums)
-        cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
-        const DevWalker d = a.walkers[w];
-        const long long total = (long long)a.nsweeps * d.n;
-        const int c = a.q_prog[w];
-        const long long chunk = d.n >= a.whole_n ? total : (long long)a.chunk_moves;
-        const long long m0 = (long long)(c & (DEAD - 1)) * chunk;
-        const long long m1 = min(total, m0 + chunk);
-        bool ok = true;
-        if (!(c & DEAD))
-            ok = a.gmem ? run_range<T, MEXP, SYM, TPW, true>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total, jm)
-                        : run_range<T, MEXP, SYM, TPW, false>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total, jm);
-        __threadfence();  // this thread's stores of the walker state, before it is handed on
-        group_sync<TPW>(1 + g);
-        if (gtid == 0) {
-            a.q_prog[w] = (c + 1) | (ok ? 0 : DEAD);
-            __threadfence();
-            if (m1 < total) queue_push(a, w);
+    persistent_loop<T, MEXP, SYM, TPW>(a, mem, g, gtid, jm);
+}
+
+// ----------------------------------------------------------------------------------------------
+// Uneven batches with dominant walkers (FP32, exponent 5, symmetrised u): one CTA of TPWB threads
+// per SM.  First the whole CTA serves the dominant walkers (`big`, the first big.W entries of the
+// processing order), one whole call each, taken from a counter; then it splits into TPWB / TPWS
+// groups that take the other walkers (`a`) from the queue in chunks.  The dominant walkers' moves
+// are the longest sequential work of the call, so they get the most threads per move; the others
+// keep the group size that suits them.
+// ----------------------------------------------------------------------------------------------
+template <typename T, int MEXP, bool SYM, int TPWB, int TPWS>
+__global__ void __launch_bounds__(TPWB, TPWB <= 256 ? 2 : 1) sweep_mixed_kernel(SweepArgs a, SweepArgs big,
+                                                                                unsigned *big_next)
+{
+    static_assert(TPWB % TPWS == 0 && TPWB / TPWS <= 15, "groups of the second phase");
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned jm = 0;
+    {
+        GroupMem<T> mem;
+        mem.bind(smem, big.stride, TPWB, big.tile == 1);
+        if (big.tile == 2) mem.use_global_drift(big.fscr + (size_t)3 * big.stride * blockIdx.x, big.stride);
+        const int gtid = threadIdx.x;
+        for (;;) {
+            if (gtid == 0) *mem.bc = (int)atomicAdd(big_next, 1u);
+            group_sync<TPWB>(1);
+            const int i = *mem.bc;
+            group_sync<TPWB>(1);
+            if (i >= big.W) break;
+            const DevWalker d = big.walkers[big.order[i]];
+            run_range<T, MEXP, SYM, TPWB, false>(big, d, mem, gtid, 1, 0, (long long)big.nsweeps * d.n, true, jm);
+            group_sync<TPWB>(1);
         }
     }
+    __syncthreads();
+    const int g = threadIdx.x / TPWS, gtid = threadIdx.x % TPWS;
+    GroupMem<T> mem;
+    mem.bind(smem + (size_t)g * group_smem<T>(a.stride, TPWS, a.tile == 1), a.stride, TPWS, a.tile == 1);
+    if (a.tile == 2) mem.use_global_drift(a.fscr + (size_t)3 * a.stride * (blockIdx.x * a.G + g), a.stride);
+    persistent_loop<T, MEXP, SYM, TPWS>(a, mem, g, gtid, jm);
 }
 
 // ----------------------------------------------------------------------------------------------

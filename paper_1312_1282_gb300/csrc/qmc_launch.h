@@ -27,6 +27,12 @@ cudaError_t occupancy_sweep_f32_small(int tpw, Variant v, int block, size_t smem
 cudaError_t occupancy_sweep_f32_big(int tpw, Variant v, int block, size_t smem, int *ctas);
 cudaError_t occupancy_sweep_f64_small(int tpw, Variant v, int block, size_t smem, int *ctas);
 cudaError_t occupancy_sweep_f64_big(int tpw, Variant v, int block, size_t smem, int *ctas);
+// uneven batches with dominant walkers: FP32, exponent 5, symmetrised u; dominant walkers on whole
+// CTAs of MIXED_TPWB threads, the others on groups of tpw_small (64 or 128) threads
+constexpr int MIXED_TPWB = 256;
+cudaError_t launch_sweep_mixed(int tpw_small, int grid, size_t smem, cudaStream_t st, const SweepArgs &a,
+                               const SweepArgs &big, unsigned *big_next);
+cudaError_t occupancy_sweep_mixed(int tpw_small, size_t smem, int *ctas);
 cudaError_t launch_queue_init(const int *order, int W, uint2 *slots, int *prog, unsigned *head, unsigned *tail,
                               cudaStream_t st);
 

@@ -233,6 +233,38 @@ def test_dominant_walker_takes_the_whole_call():
         assert acc[w, 7] == oacc[7] and acc[w, 6] == oacc[6]
 
 
+@pytest.mark.parametrize("tpw", [64, 128])
+def test_mixed_sweep_matches_oracle_and_energy_pass(tpw):
+    """FP32 uneven batch with a dominant walker: the mixed kernel runs it on a whole CTA of 256
+    threads and the other walkers on groups of tpw threads from the queue.  Chains as the oracle's
+    decision by decision (except near ties), the energy samples as the stand-alone pass."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    ns = [600, 600] + [64] * (nsm + 30)
+    W = len(ns)
+    P = lattice_batch(ns, q.QMC_FP32, seed=10)
+    opt = q.options(precision=q.QMC_FP32, recompute_every=0, threads_per_walker=tpw)
+    lp = zeros(W)
+    q.qmc_log_psi(P.d, opt, P.pos, lp)
+    sw, acc = zeros(W, torch.int64), zeros((W, 8))
+    q.qmc_sweep(P.d, opt, P.pos, lp, sw, 0x313, 2, 2, acc)
+    e = zeros((W, 5))
+    q.qmc_local_energy(P.d, q.options(precision=q.QMC_FP32), P.pos, e)
+    assert q.qmc_status(timeout_ms=120000) == 0
+    a = acc.cpu().numpy()
+    assert np.all(sw.cpu().numpy() == 2) and np.all(a[:, 6] == 1)
+    en = e.cpu().numpy()
+    for w in range(W):
+        assert np.all(np.abs(a[w, [2, 3, 4, 5, 0]] - en[w]) <= 1e-5 * energy_scale(en[w])), w
+    agree = 0
+    for w in (0, 2, W - 1):
+        pos, _, _, oacc, mg = _oracle_chain(P, w, 0x313, 2, 0, opt, margins=True)
+        if a[w, 7] == oacc[7] and np.abs(P.positions(w) - pos).max() < 1e-3:
+            agree += 1
+        else:
+            assert np.abs(mg).min() < 1e-4, (w, np.abs(mg).min())
+    assert agree >= 2
+
+
 def test_persistent_queue_mode_survives_a_faulted_walker():
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     W = nsm + 5
