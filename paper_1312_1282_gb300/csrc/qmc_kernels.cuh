@@ -1352,7 +1352,7 @@ __device__ __forceinline__ void queue_push(const SweepArgs &a, int w)
 
 // Persistent mode: take ready walkers from the FIFO, advance each by one chunk, put it back.
 template <typename T, int MEXP, bool SYM, int TPW>
-__device__ void persistent_loop(const SweepArgs &a, GroupMem<T> &mem, int g, int gtid, unsigned &jm)
+__device__ __forceinline__ void persistent_loop(const SweepArgs &a, GroupMem<T> mem, int g, int gtid, unsigned &jm)
 {
     constexpr int DEAD = 1 << 30;
     for (;;) {
