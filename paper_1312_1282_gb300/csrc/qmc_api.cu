@@ -509,7 +509,6 @@ int mixed_sweep(const qmc_walker_desc *d, int W, const qmc_options *o, const Pla
     small.gmem = 0;
     small.dynamic = 1;
     small.chunk_moves = (int)chunk;
-    small.whole_n = INT_MAX;
     small.q_total = (unsigned)total;
     small.q_head = P.q_ctr;
     small.q_tail = P.q_ctr + 1;
@@ -573,7 +572,6 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     a.err = p.ds->err;
     a.dynamic = 0;
     a.chunk_moves = 0;
-    a.whole_n = INT_MAX;
     a.q_total = 0;
     a.q_head = a.q_tail = nullptr;
     a.q_slots = nullptr;
@@ -604,10 +602,10 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
             occ_cache[okey] = ctas;
         }
         const long long chunk = std::max(128, ((P.maxn + QMC_CHUNK_DIV - 1) / QMC_CHUNK_DIV + 31) / 32 * 32);
-        // Walkers whose own pair work is at least the mean load of a resident group and four times
-        // the batch mean bound the call by their sequential moves alone: they take the whole call
-        // as one chunk instead of waiting in the queue between chunks (uneven batches; in a batch
-        // of equal walkers nobody qualifies)
+        // Dominant walkers: pair work alone at least the mean load of a resident group and four
+        // times the batch mean.  Their sequential moves bound the call, so waiting in the queue
+        // between chunks would lengthen that bound: the mixed kernel runs each for the whole call
+        // (in a batch of equal walkers nobody qualifies)
         const long long slots = (long long)std::max(ctas, 1) * p.ds->nsm * G;
         double work_sum = 0;
         for (int w = 0; w < W; ++w) work_sum += (double)d[w].n * d[w].n;
@@ -617,10 +615,7 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
             if (wk >= work_sum / (double)slots && wk >= 4.0 * work_sum / W) whole_n = std::min(whole_n, d[w].n);
         }
         long long total = 0;
-        for (int w = 0; w < W; ++w) {
-            const long long tw = (long long)nsweeps * d[w].n;
-            total += d[w].n >= whole_n ? 1 : (tw + chunk - 1) / chunk;
-        }
+        for (int w = 0; w < W; ++w) total += ((long long)nsweeps * d[w].n + chunk - 1) / chunk;
         if (whole_n < INT_MAX && ctas > 0) {
             const int mrc = mixed_sweep(d, W, o, P, p, tpw, v, whole_n, nsweeps, a, st);
             if (mrc != -1) return mrc;  // launched (or failed); -1: the batch does not suit it
@@ -631,7 +626,6 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
         if (ctas > 0 && !even && total < (1ll << 31)) {
             a.dynamic = 1;
             a.chunk_moves = (int)chunk;
-            a.whole_n = whole_n;
             a.q_total = (unsigned)total;
             a.q_head = P.q_ctr;
             a.q_tail = P.q_ctr + 1;
@@ -1043,7 +1037,6 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     a.err = err ? reinterpret_cast<unsigned *>(err) : d_err;
     a.dynamic = 0;  // one walker per group: no queue memory needed
     a.chunk_moves = 0;
-    a.whole_n = INT_MAX;
     a.q_total = 0;
     a.q_head = a.q_tail = nullptr;
     a.q_slots = nullptr;

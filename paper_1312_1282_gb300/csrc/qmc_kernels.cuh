@@ -113,8 +113,7 @@ struct SweepArgs {
     // persistent mode: walkers circulate through a FIFO of ready walkers in chunks of moves
     int dynamic;             // 0: one walker per thread group for the whole call
     int chunk_moves;         // moves per chunk (a multiple of 32)
-    int whole_n;             // walkers of at least whole_n atoms take the whole call as one chunk
-    unsigned q_total;        // chunks of all walkers: sum over w of ceil(nsweeps n_w / chunk of w)
+    unsigned q_total;        // chunks of all walkers: sum over w of ceil(nsweeps n_w / chunk_moves)
     unsigned *q_head, *q_tail;
     uint2 *q_slots;          // [W] {sequence, walker table index}
     int *q_prog;             // [W] chunks done (bit 30: walker faulted, its chunks are skipped)
@@ -1366,9 +1365,8 @@ __device__ __forceinline__ void persistent_loop(const SweepArgs &a, GroupMem<T> 
         const DevWalker d = a.walkers[w];
         const long long total = (long long)a.nsweeps * d.n;
         const int c = a.q_prog[w];
-        const long long chunk = d.n >= a.whole_n ? total : (long long)a.chunk_moves;
-        const long long m0 = (long long)(c & (DEAD - 1)) * chunk;
-        const long long m1 = min(total, m0 + chunk);
+        const long long m0 = (long long)(c & (DEAD - 1)) * a.chunk_moves;
+        const long long m1 = min(total, m0 + a.chunk_moves);
         bool ok = true;
         if (!(c & DEAD))
             ok = a.gmem ? run_range<T, MEXP, SYM, TPW, true>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total, jm)

@@ -206,9 +206,9 @@ def test_persistent_queue_mode_matches_oracle_and_static_path():
         np.testing.assert_allclose(acc[w, :6], oacc[:6], rtol=1e-10, atol=1e-9)
 
 
-def test_dominant_walker_takes_the_whole_call():
-    """An uneven batch in which one walker's pair work dominates: that walker runs its whole call
-    as one chunk of the persistent queue, the others in chunks.  Chains as the oracle's (FP64, bit
+def test_uneven_batch_with_a_dominant_walker():
+    """An uneven batch in which one walker's pair work dominates, in FP64 (the persistent queue;
+    FP32 batches of this kind run the mixed kernel, tested below).  Chains as the oracle's (bit
     for bit) and as the one-walker-per-group path."""
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     ns = [600] + [64] * (nsm + 20)
