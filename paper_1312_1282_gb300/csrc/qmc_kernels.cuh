@@ -10,8 +10,9 @@
 // 32).  For one move every thread of the group evaluates the old and new pair terms of its
 // partner chunks j = 4c..4c+3, c = gtid, gtid + TPW, ...; the group sums them (warp butterfly,
 // then one named barrier), and every thread takes the same accept/reject decision.  The owner of
-// the moved atom's chunk writes its new coordinates; all other threads keep a register copy of
-// the last accepted move, so a move needs exactly one group barrier (none for TPW = 32).
+// the moved atom's chunk writes its new coordinates; all other threads keep a private copy of
+// the last batch's accepted moves, so a batch of moves (two in FP32 for groups of 64 threads or
+// more, one otherwise) needs exactly one group barrier (none for TPW = 32).
 #pragma once
 
 #include <cuda/atomic>
@@ -1381,10 +1382,9 @@ __device__ __forceinline__ void persistent_loop(const SweepArgs &a, GroupMem<T> 
     }
 }
 
-// CTAs hold up to 256 threads (TPW <= 256) or exactly one group; at least 1024 resident threads
-// per SM, i.e. at most 64 registers per thread.
-// Up to 128 registers per thread (at least 512 resident threads per SM) except for groups of
-// 1024 threads, which keep 64.
+// CTAs hold up to 256 threads (TPW <= 256) or exactly one group.  Launch bounds: at least 512
+// resident threads per SM, i.e. up to 128 registers per thread, except for groups of 1024
+// threads, which keep 64.
 template <int TPW> constexpr int cta_bound() { return TPW > 256 ? TPW : 256; }
 template <int TPW> constexpr int min_blocks() { return TPW <= 256 ? 2 : 1; }
 
