@@ -136,16 +136,39 @@ def options(precision=QMC_FP32, proposal=QMC_CUBE, sym=1, sequential=0, hbar2_ov
 # ---------------------------------------------------------------------------------------------
 # one-to-one wrappers of the C ABI
 # ---------------------------------------------------------------------------------------------
+_NVTX = os.environ.get("QMC_NVTX") == "1"
 
+
+def _traced(fn):
+    """With QMC_NVTX=1 in the environment, each call is an NVTX range named after the C entry
+    point (visible to Nsight tools; a no-op otherwise)."""
+    if not _NVTX:
+        return fn
+    import functools
+
+    @functools.wraps(fn)
+    def wrapper(*args, **kwargs):
+        torch.cuda.nvtx.range_push(fn.__name__)
+        try:
+            return fn(*args, **kwargs)
+        finally:
+            torch.cuda.nvtx.range_pop()
+
+    return wrapper
+
+
+@_traced
 def qmc_init_walkers(d, seed, jitter_sigma, opt, pos, stream=None):
     return _check(lib().qmc_init_walkers(d, len(d), seed, jitter_sigma, C.byref(opt), _ptr(pos), _stream(stream)))
 
 
+@_traced
 def qmc_sweep(d, opt, pos, logpsi, sweep, seed, nsweeps, energy_every, accum, stream=None):
     return _check(lib().qmc_sweep(d, len(d), C.byref(opt), _ptr(pos), _ptr(logpsi), _ptr(sweep), seed, nsweeps,
                                   energy_every, _ptr(accum), _stream(stream)))
 
 
+@_traced
 def qmc_sweep_static(d, opt, pos, logpsi, sweep, seed, nsweeps, energy_every, accum, err=None, stream=None):
     """qmc_sweep without any device allocation by the library (fixed scratch array; at most
     QMC_STATIC_MAX_WALKERS walkers; calls overlapping on the GPU must not be issued)."""
@@ -153,23 +176,28 @@ def qmc_sweep_static(d, opt, pos, logpsi, sweep, seed, nsweeps, energy_every, ac
                                          nsweeps, energy_every, _ptr(accum), _ptr(err), _stream(stream)))
 
 
+@_traced
 def qmc_local_energy(d, opt, pos, out, stream=None):
     return _check(lib().qmc_local_energy(d, len(d), C.byref(opt), _ptr(pos), _ptr(out), _stream(stream)))
 
 
+@_traced
 def qmc_energy_grad(d, opt, pos, out, stream=None):
     return _check(lib().qmc_energy_grad(d, len(d), C.byref(opt), _ptr(pos), _ptr(out), _stream(stream)))
 
 
+@_traced
 def qmc_log_psi(d, opt, pos, out, stream=None):
     return _check(lib().qmc_log_psi(d, len(d), C.byref(opt), _ptr(pos), _ptr(out), _stream(stream)))
 
 
+@_traced
 def qmc_trial_delta(d, opt, pos, s, delta, M, out, stream=None):
     return _check(lib().qmc_trial_delta(d, len(d), C.byref(opt), _ptr(pos), _ptr(s), _ptr(delta), M, _ptr(out),
                                         _stream(stream)))
 
 
+@_traced
 def qmc_pair_hist(d, opt, pos, nbins, rmax, hist, stream=None):
     return _check(lib().qmc_pair_hist(d, len(d), C.byref(opt), _ptr(pos), nbins, rmax, _ptr(hist), _stream(stream)))
 
@@ -184,6 +212,7 @@ def pair_correlation(counts, n, L, rmax, samples):
     return 0.5 * (edges[1:] + edges[:-1]), counts / (samples * n * (n - 1) / 2.0 * shell)
 
 
+@_traced
 def qmc_autotune(d, opt, pos, stream=None) -> int:
     t = C.c_int(0)
     _check(lib().qmc_autotune(d, len(d), C.byref(opt), _ptr(pos), _stream(stream), C.byref(t)))
