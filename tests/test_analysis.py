@@ -90,3 +90,20 @@ def test_penalty_limits():
                 if alpha >= 1:
                     p = an.time_per_error(m, mc, 1, alpha, masked=True) / best_mask
                     assert 1 - 1e-12 <= p <= max(alpha / m, m / alpha)
+
+
+def test_pair_correlation_of_an_ideal_gas_is_one():
+    """pair_correlation's normalisation: uniformly random points (an ideal gas) have g(r) = 1; the
+    counts come from the oracle's brute-force histogram."""
+    import oracle
+    from paper_1312_1282_gb300 import pair_correlation
+    n, L, nbins, samples = 200, 20.0, 10, 40
+    rng = np.random.default_rng(12)
+    counts = np.zeros(nbins)
+    for _ in range(samples):
+        counts += oracle.pair_hist(rng.uniform(0, L, size=(3, n)), L, nbins, L / 2)
+    r, g = pair_correlation(counts, n, L, L / 2, samples)
+    assert np.allclose(r, (np.arange(nbins) + 0.5) * L / 2 / nbins)
+    # Poisson error of each bin's count, relative: 1/sqrt(count)
+    err = 1 / np.sqrt(np.maximum(counts, 1))
+    assert np.all(np.abs(g[1:] - 1) < 4 * err[1:] + 0.01), g
