@@ -490,11 +490,14 @@ def run_large(args):
     import paper_1312_1282_gb300 as q
     torch.cuda.set_device(0)
     n, S = args.large_n, args.large_sweeps
-    W = torch.cuda.get_device_properties(0).multi_processor_count
+    W = args.large_walkers or torch.cuda.get_device_properties(0).multi_processor_count
     L = qi.box_side(n, qi.RHO_HE)
     pad = qi.pad4(n)
     d = q.descs([(n, pad, w * 3 * pad, w, L, 0.0, qi.B_HE, 5.0, 0.8) for w in range(W)])
-    opt = q.options(precision=q.QMC_FP32, recompute_every=50)
+    # --large-plain: macroupdates only (no energy samples, no ln psi recomputes), the paper's
+    # measure of Sec. 7.4; with few walkers this runs each walker on a thread-block cluster
+    opt = q.options(precision=q.QMC_FP32, recompute_every=0 if args.large_plain else 50)
+    E = 0 if args.large_plain else S
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     lp = torch.zeros(W, dtype=torch.float64, device="cuda")
     sw = torch.zeros(W, dtype=torch.int64, device="cuda")
@@ -514,7 +517,7 @@ def run_large(args):
         a, b = _events(torch)
         c, e = _events(torch)
         a.record()
-        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, S, S, acc)
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, S, E, acc)
         b.record()
         c.record()
         q.qmc_energy_grad(d, opt, pos, grad)
@@ -529,11 +532,15 @@ def run_large(args):
     dE_db = 2 * (np.mean(EL * Ob) - EL.mean() * Ob.mean()) / n
     dE_dm = 2 * (np.mean(EL * Om) - EL.mean() * Om.mean()) / n
     pe = 2.0 * n * (n - 1) * W * S * args.steps
-    print(json.dumps({"config": f"N={n}, one walker per SM, {S} sweeps + adjoint per step", "walkers": W,
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    cluster = args.large_plain and 2 * W <= nsm and n >= 4096  # the library's cluster-sweep rule
+    print(json.dumps({"config": f"N={n}, {W} walkers, {S} sweeps + adjoint per step", "walkers": W,
+                      "sweep_path": "thread-block cluster per walker" if cluster else "one CTA per walker",
                       "hbm_walkers": n > q.qmc_capacity(q.QMC_FP32), "threads_per_walker": tpw,
                       "pair_evals_per_s": pe / (t_sw * 1e-3), "ms_per_macroupdate_all_walkers": t_sw / args.steps / S,
                       "ms_per_step_sweeps": t_sw / args.steps, "ms_per_adjoint": t_gr / args.steps,
-                      "E_per_atom": float(acc[:, 0].sum() / acc[:, 6].sum() / n),
+                      "E_per_atom": float(acc[:, 0].sum() / acc[:, 6].sum() / n) if E else None,
+                      "acceptance": float(acc[:, 7].sum() / (W * n * (S * args.steps + args.warmup))) if E == 0 else None,
                       "dE_per_atom_db_K_per_A": dE_db, "dE_per_atom_dm": dE_dm}), flush=True)
     return 0
 
@@ -799,6 +806,8 @@ def main():
     ap.add_argument("--large-n", type=int, default=10000, help="large: atoms per walker")
     ap.add_argument("--c3-fp64-sweeps", type=int, default=600, help="c3: measured FP64 sweeps")
     ap.add_argument("--large-sweeps", type=int, default=20, help="large: sweeps per step")
+    ap.add_argument("--large-walkers", type=int, default=0, help="large: walkers (0: one per SM)")
+    ap.add_argument("--large-plain", action="store_true", help="large: sweeps only (no energy, no ln psi recompute)")
     ap.add_argument("--t2e-seconds", type=float, default=3.0, help="t2e: production seconds per N and m")
     ap.add_argument("--t2e-sizes", default="", help="t2e: comma-separated N (default 128..4000)")
     ap.add_argument("--config", default="headline", choices=["headline", "uneven", "large", "fp64cmp", "t2e", "c3"],

@@ -19,6 +19,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "qmc_cluster.cuh"
 #include "qmc_launch.h"
 
 using namespace qmc;
@@ -534,6 +535,57 @@ int mixed_sweep(const qmc_walker_desc *d, int W, const qmc_options *o, const Pla
     return QMC_OK;
 }
 
+// Few walkers of very large N (at most one per two SMs, N >= 4096): each walker runs on a
+// thread-block cluster of C CTAs, one per SM (qmc_cluster.cuh).  FP32 exponent-5 symmetrised
+// walkers, calls without energy samples or ln psi recomputes.  Returns -1 (nothing launched) when
+// the batch does not suit it.  QMC_CLUSTER=0 turns it off; QMC_CLUSTER=1 uses it for every
+// batch that suits it apart from the size rule (used by the tests).
+int cluster_sweep(const qmc_walker_desc *d, int W, const qmc_options *o, const Plan &P, Prep &p, void *pos,
+                  double *logpsi, uint64_t *sweep, uint64_t seed, int nsweeps, int energy_every, double *accum,
+                  cudaStream_t st)
+{
+    static const int mode = [] {
+        const char *e = std::getenv("QMC_CLUSTER");
+        return e ? (e[0] == '0' ? 0 : (e[0] == '1' ? 2 : 1)) : 1;
+    }();
+    if (mode == 0 || o->precision != QMC_FP32 || variant_of(P, o) != V5S || energy_every != 0 ||
+        o->recompute_every != 0)
+        return -1;
+    const int nsm = p.ds->nsm;
+    if (mode == 1 && (2 * W > nsm || P.maxn < 4096)) return -1;
+    int C = CLUSTER_MAX;
+    while (C > 2 && W * C > nsm) C /= 2;
+    int slice = ((P.maxn + C - 1) / C + 3) & ~3;
+    while (cluster_smem(slice) > MAX_SMEM && C < CLUSTER_MAX) {
+        C *= 2;
+        slice = ((P.maxn + C - 1) / C + 3) & ~3;
+    }
+    const size_t smem = cluster_smem(slice);
+    if (smem > MAX_SMEM) return -1;
+    int clusters = 0;
+    cudaError_t e = cluster_capacity(C, smem, &clusters);
+    if (e != cudaSuccess) return cuda_fail(e, "cluster occupancy query");
+    if (clusters < 1) return -1;
+    ClusterArgs a;
+    a.walkers = P.d_walkers;
+    a.W = W;
+    a.C = C;
+    a.slice = slice;
+    a.pos = pos;
+    a.logpsi = logpsi;
+    a.sweep = reinterpret_cast<unsigned long long *>(sweep);
+    a.accum = accum;
+    a.seed = seed;
+    a.nsweeps = nsweeps;
+    a.proposal = o->proposal;
+    a.sequential = o->sequential;
+    a.err = p.ds->err;
+    e = launch_sweep_cluster(W * C, smem, st, a);
+    if (e != cudaSuccess) return cuda_fail(e, "cluster sweep launch");
+    g_launches.fetch_add(1);
+    return QMC_OK;
+}
+
 int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos, double *logpsi, uint64_t *sweep,
                uint64_t seed, int nsweeps, int energy_every, double *accum, cudaStream_t st, int tpw_force)
 {
@@ -548,6 +600,10 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     const Plan &P = *p.plan;
     const int tpw = tpw_force ? tpw_force : choose_tpw(P, o, p.dev, p.ds->nsm);
     if (nsweeps == 0) return QMC_OK;
+    if (!tpw_force) {
+        const int crc = cluster_sweep(d, W, o, P, p, pos, logpsi, sweep, seed, nsweeps, energy_every, accum, st);
+        if (crc != -1) return crc;
+    }
     const int G = choose_groups(P, o->precision, tpw, p.ds->nsm);
     const Shape sh = shape_of(P, o->precision, tpw, G, true, true);
     SweepArgs a;
