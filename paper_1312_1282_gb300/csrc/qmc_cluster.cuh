@@ -2,15 +2,16 @@
 //
 // With fewer walkers than SMs, one CTA per walker leaves most of the GPU idle (the paper's own
 // 40 960-atom run used 13 walkers).  Here each walker is served by a cluster of C CTAs (C = 2, 4
-// or 8, one per SM): CTA r holds atoms [rS, rS + S) of the walker in its shared memory.  For a
-// move every CTA draws the same random numbers (the counters of Sec. 5.2, as in the one-CTA
-// sweep), reads the moved atom's position from its owner's shared memory through distributed
-// shared memory (DSMEM), evaluates the partner terms of Eq. (JastrowUpdate) over its slice, and
-// the C partial sums are exchanged: every CTA's thread 0 stores its partial into each CTA's slot
-// and arrives on each CTA's mbarrier (release at cluster scope); every thread waits on its own
-// CTA's mbarrier (acquire, bounded) and adds the C partials in rank order, so all CTAs take the
-// same decision (Eq. Decision).  The owner of the moved atom writes its new position; all threads
-// keep a copy of the last accepted move for the one read that may precede that write's
+// or 8, one per SM): CTA r holds atoms [rS, rS + S) of the walker in its shared memory.  Moves
+// go in batches of CLUSTER_KB.  Every CTA draws the same random numbers (the counters of
+// Sec. 5.2, as in the one-CTA sweep), reads the moved atoms' positions from their owners' shared
+// memory through distributed shared memory (DSMEM), evaluates the partner terms of
+// Eq. (JastrowUpdate) over its slice, and the C partial sums of each move are exchanged: threads
+// 0 .. CLUSTER_KB-1 of every CTA store their partial into each CTA's slot and arrive on each
+// CTA's mbarrier (release at cluster scope); every thread waits on its own CTA's mbarrier
+// (acquire, bounded) and adds the C partials in rank order, so all CTAs take the same decisions
+// (Eq. Decision).  The owners of the moved atoms write their new positions; all threads keep a
+// copy of the previous batch's accepted moves for the reads that may precede those writes'
 // visibility.  FP32, exponent 5, symmetrised u; calls without energy samples or ln psi
 // recomputes (those run as separate passes).
 #pragma once
@@ -106,25 +107,42 @@ __device__ __forceinline__ void cluster_sync_all()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// shared memory of one CTA: x | y | z slices (slice floats each), 32 warp partials, 2 x 8
-// exchange slots, 2 mbarriers
-__host__ __device__ constexpr size_t cluster_smem(int slice) { return (size_t)3 * slice * 4 + 128 + 64 + 16; }
+// Moves per exchange.  A batch of CLUSTER_KB consecutive moves of distinct atoms is evaluated
+// against the configuration at the start of the batch, as in the one-CTA batched moves: every CTA
+// sums the partner terms of all the batch's moves over its slice (the batch's atoms masked), one
+// exchange carries the CLUSTER_KB partial sums, and the decisions are taken in order with the
+// moved atoms' own terms and the cross terms D_ik, which every warp computes (one pair per lane).
+// One cluster round trip per batch instead of one per move.
+#ifndef QMC_CLUSTER_KB
+#define QMC_CLUSTER_KB 4
+#endif
+constexpr int CLUSTER_KB = QMC_CLUSTER_KB;
+static_assert(CLUSTER_KB == 1 || CLUSTER_KB == 2 || CLUSTER_KB == 4, "moves per exchange: 1, 2 or 4");
+
+// shared memory of one CTA: x | y | z slices (slice floats each), CLUSTER_KB x 32 warp partials,
+// 2 x CLUSTER_KB x 8 exchange slots, 2 mbarriers
+__host__ __device__ constexpr size_t cluster_smem(int slice)
+{
+    return (size_t)3 * slice * 4 + (size_t)CLUSTER_KB * 32 * 4 + (size_t)2 * CLUSTER_KB * 8 * 4 + 16;
+}
 
 template <int TPW>
 __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NW = TPW / 32;
+    constexpr int K = CLUSTER_KB;
     const int gtid = threadIdx.x, lane = gtid & 31, warp = gtid >> 5;
     const unsigned rank = cluster_rank();
     const int C = a.C;
     float *sx = reinterpret_cast<float *>(smem), *sy = sx + a.slice, *sz = sy + a.slice;
-    float *red = sz + a.slice;
-    float *part = red + 32;
-    unsigned long long *mb = reinterpret_cast<unsigned long long *>(part + 16);
+    float *red = sz + a.slice;  // [K][NW]
+    float *part = red + K * 32;  // [2][K][8]
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(part + 2 * K * 8);
     if (gtid == 0) {
-        mb_init(mb, (unsigned)C);
-        mb_init(mb + 1, (unsigned)C);
+        // every exchange: threads 0 .. K-1 of each of the C CTAs arrive once
+        mb_init(mb, (unsigned)(C * K));
+        mb_init(mb + 1, (unsigned)(C * K));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -142,26 +160,36 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
     J.init(d);
 
     unsigned jx = 0;  // exchanges so far: slot set jx & 1, phase parity (jx >> 1) & 1
-    // the sum over the cluster of one value per thread, identical in every CTA (rank order)
-    auto exchange = [&](float v, float &total) -> bool {
-        v = warp_sum(v);
-        if (lane == 0) red[warp] = v;
+    // the sums over the cluster of K values per thread, identical in every CTA (rank order):
+    // warp sums, then threads 0 .. K-1 each add one value over the warps, store it into every
+    // CTA's slot and arrive on every CTA's mbarrier (release at cluster scope)
+    auto exchange = [&](float (&v)[K]) -> bool {
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = warp_sum(v[i]);
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < K; ++i) red[i * NW + warp] = v[i];
         __syncthreads();
         const unsigned ph = jx & 1u, par = (jx >> 1) & 1u;
         ++jx;
-        if (gtid == 0) {
-            float s = red[0];
+        if (gtid < K) {
+            float s = red[gtid * NW];
 #pragma unroll
-            for (int w = 1; w < NW; ++w) s += red[w];
+            for (int w = 1; w < NW; ++w) s += red[gtid * NW + w];
+            float *slot = &part[(ph * K + gtid) * 8 + rank];
             for (int r = 0; r < C; ++r) {
-                st_cluster(map_rank(&part[ph * 8 + rank], (unsigned)r), s);
+                st_cluster(map_rank(slot, (unsigned)r), s);
                 mb_arrive_remote(map_rank(&mb[ph], (unsigned)r));
             }
         }
         if (!mb_wait_cluster(&mb[ph], par, a.err)) return false;
-        float t = part[ph * 8];
-        for (int r = 1; r < C; ++r) t += part[ph * 8 + r];
-        total = t;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const float *p = &part[(ph * K + i) * 8];
+            float t = p[0];
+            for (int r = 1; r < C; ++r) t += p[r];
+            v[i] = t;
+        }
         return true;
     };
 
@@ -182,35 +210,197 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
         sy[i] = y;
         sz[i] = z;
     }
-    float nbad = 0.f;
-    bool ok = exchange((float)bad, nbad);
-    if (ok && nbad != 0.f) {
-        if (gtid == 0 && rank == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
-        ok = false;
+    bool ok;
+    {
+        float v[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = i == 0 ? (float)bad : 0.f;
+        ok = exchange(v);
+        if (ok && v[0] != 0.f) {
+            if (gtid == 0 && rank == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
+            ok = false;
+        }
     }
 
     LogPsiAcc<float> lp;
     lp.set(a.logpsi[d.slot]);
     const unsigned long long k0 = a.sweep[d.slot];
     int nacc = 0;
-    int rs = -1;  // the last accepted move: atom and new position (register copy)
-    float rx = 0.f, ry = 0.f, rz = 0.f;
+    // the accepted moves of the previous exchange (atom, or -1, and new position): their owners'
+    // writes become visible to other threads only after the next exchange
+    int ps[K];
+    float pbx[K], pby[K], pbz[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        ps[q] = -1;
+        pbx[q] = pby[q] = pbz[q] = 0.f;
+    }
     Packed5 P;
     P.init(J);
+    // the block's per-lane move parameters (atom, displacement, ln xi)
+    int my_s = 0;
+    float mdx = 0.f, mdy = 0.f, mdz = 0.f, mxi = 0.f;
+
+    // moves tt .. tt+KK-1 of the current block (distinct atoms) with one exchange
+    auto moves = [&](auto kk_tag, int tt) -> bool {
+        constexpr int KK = decltype(kk_tag)::value;
+        int s[KK], own[KK], ls[KK], cs[KK];
+        float ax[KK], ay[KK], az[KK], bx[KK], by[KK], bz[KK], lxi[KK];
+#pragma unroll
+        for (int i = 0; i < KK; ++i) {
+            s[i] = __shfl_sync(FULL, my_s, tt + i);
+            own[i] = s[i] / S;
+            ls[i] = s[i] - own[i] * S;
+            lxi[i] = __shfl_sync(FULL, mxi, tt + i);
+            if (own[i] == (int)rank) {
+                ax[i] = sx[ls[i]];
+                ay[i] = sy[ls[i]];
+                az[i] = sz[ls[i]];
+            } else {
+                ax[i] = ld_cluster(map_rank(&sx[ls[i]], (unsigned)own[i]));
+                ay[i] = ld_cluster(map_rank(&sy[ls[i]], (unsigned)own[i]));
+                az[i] = ld_cluster(map_rank(&sz[ls[i]], (unsigned)own[i]));
+            }
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                if (ps[q] == s[i]) {
+                    ax[i] = pbx[q];
+                    ay[i] = pby[q];
+                    az[i] = pbz[q];
+                }
+            bx[i] = wrap(ax[i] + __shfl_sync(FULL, mdx, tt + i), L);
+            by[i] = wrap(ay[i] + __shfl_sync(FULL, mdy, tt + i), L);
+            bz[i] = wrap(az[i] + __shfl_sync(FULL, mdz, tt + i), L);
+            cs[i] = own[i] == (int)rank ? ls[i] >> 2 : -1;
+        }
+        // partner terms over this slice, the batch's atoms masked (they add zero)
+        float2 nax[KK], nay[KK], naz[KK], nbx[KK], nby[KK], nbz[KK], acco[KK], accn[KK];
+#pragma unroll
+        for (int i = 0; i < KK; ++i) {
+            nax[i] = make_float2(-ax[i], -ax[i]);
+            nay[i] = make_float2(-ay[i], -ay[i]);
+            naz[i] = make_float2(-az[i], -az[i]);
+            nbx[i] = make_float2(-bx[i], -bx[i]);
+            nby[i] = make_float2(-by[i], -by[i]);
+            nbz[i] = make_float2(-bz[i], -bz[i]);
+            acco[i] = make_float2(0.f, 0.f);
+            accn[i] = make_float2(0.f, 0.f);
+        }
+        for (int c = gtid; c < nv; c += TPW) {
+            float4 X = reinterpret_cast<const float4 *>(sx)[c];
+            float4 Y = reinterpret_cast<const float4 *>(sy)[c];
+            float4 Z = reinterpret_cast<const float4 *>(sz)[c];
+#pragma unroll
+            for (int i = 0; i < KK; ++i)
+                if (c == cs[i]) {
+                    const int e = ls[i] - 4 * c;
+                    Vec<float>::set(X, e, qnan<float>());
+                    Vec<float>::set(Y, e, qnan<float>());
+                    Vec<float>::set(Z, e, qnan<float>());
+                }
+            const float2 xa = make_float2(X.x, X.y), xb = make_float2(X.z, X.w);
+            const float2 ya = make_float2(Y.x, Y.y), yb = make_float2(Y.z, Y.w);
+            const float2 za = make_float2(Z.x, Z.y), zb = make_float2(Z.z, Z.w);
+#pragma unroll
+            for (int i = 0; i < KK; ++i) {
+                P.acc5(__fadd2_rn(xa, nax[i]), __fadd2_rn(ya, nay[i]), __fadd2_rn(za, naz[i]), acco[i]);
+                P.acc5(__fadd2_rn(xa, nbx[i]), __fadd2_rn(ya, nby[i]), __fadd2_rn(za, nbz[i]), accn[i]);
+                P.acc5(__fadd2_rn(xb, nax[i]), __fadd2_rn(yb, nay[i]), __fadd2_rn(zb, naz[i]), acco[i]);
+                P.acc5(__fadd2_rn(xb, nbx[i]), __fadd2_rn(yb, nby[i]), __fadd2_rn(zb, nbz[i]), accn[i]);
+            }
+        }
+        float v[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < KK; ++i) v[i] = J.c * ((accn[i].x + accn[i].y) - (acco[i].x + acco[i].y));
+        // the batch's atoms as partners of its other moves: lane i KK + k (k != i) holds
+        // t_ik = u(|b_i - a_k|) - u(|a_i - a_k|) and, for i > k, the cross term
+        // D_ik = u(|b_i - b_k|) - u(|a_i - b_k|) - t_ik (atom s_k accepted before move i)
+        float tl = 0.f, dl = 0.f;
+        if constexpr (KK > 1) {
+            const int li = lane / KK, lk = lane % KK;
+            float aix = 0.f, aiy = 0.f, aiz = 0.f, bix = 0.f, biy = 0.f, biz = 0.f;
+            float akx = 0.f, aky = 0.f, akz = 0.f, bkx = 0.f, bky = 0.f, bkz = 0.f;
+#pragma unroll
+            for (int q = 0; q < KK; ++q) {
+                if (q == li) {
+                    aix = ax[q];
+                    aiy = ay[q];
+                    aiz = az[q];
+                    bix = bx[q];
+                    biy = by[q];
+                    biz = bz[q];
+                }
+                if (q == lk) {
+                    akx = ax[q];
+                    aky = ay[q];
+                    akz = az[q];
+                    bkx = bx[q];
+                    bky = by[q];
+                    bkz = bz[q];
+                }
+            }
+            if (lane < KK * KK && li != lk) {
+                tl = cross5(J, aix, aiy, aiz, bix, biy, biz, akx, aky, akz);
+                if (li > lk) dl = cross5(J, aix, aiy, aiz, bix, biy, biz, bkx, bky, bkz) - tl;
+            }
+            // sum of t_ik over k within each group of KK lanes
+#pragma unroll
+            for (int o = KK / 2; o > 0; o >>= 1) tl += __shfl_xor_sync(FULL, tl, o);
+        }
+        if (!exchange(v)) return false;
+        bool acc[KK];
+#pragma unroll
+        for (int i = 0; i < KK; ++i) {
+            float delta = v[i];
+            if constexpr (KK > 1) {
+                delta += __shfl_sync(FULL, tl, i * KK);
+#pragma unroll
+                for (int k = 0; k < i; ++k) {
+                    const float dik = __shfl_sync(FULL, dl, i * KK + k);
+                    if (acc[k]) delta += dik;
+                }
+            }
+            if (delta != delta) {
+                if (gtid == 0 && rank == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
+                return false;
+            }
+            acc[i] = 2.f * delta > lxi[i];  // Eq. (Decision)
+            if (acc[i]) {
+                if (gtid == 0 && rank == 0) lp.add(delta);
+                ++nacc;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < KK; ++q) {
+            if (acc[q] && own[q] == (int)rank && gtid == (ls[q] >> 2) % TPW) {
+                sx[ls[q]] = bx[q];
+                sy[ls[q]] = by[q];
+                sz[ls[q]] = bz[q];
+            }
+            ps[q] = acc[q] ? s[q] : -1;
+            pbx[q] = bx[q];
+            pby[q] = by[q];
+            pbz[q] = bz[q];
+        }
+#pragma unroll
+        for (int q = KK; q < K; ++q) ps[q] = -1;
+        return true;
+    };
+
     for (int it = 0; ok && it < a.nsweeps; ++it) {
         const uint32_t k = (uint32_t)(k0 + (unsigned long long)it);
         for (int t0 = 0; ok && t0 < n; t0 += 32) {
             // random numbers of moves t0 .. t0+31, one move per lane, as in the one-CTA sweep
             const uint32_t t = (uint32_t)(t0 + lane);
             const uint4 rw = philox(t, k, d.wid, ST_STEP, a.seed);
-            int my_s;
             if (a.sequential) {
                 my_s = (int)t;
             } else {
                 const uint4 ri = philox(((uint32_t)t0 >> 2) + (uint32_t)(lane >> 2), k, d.wid, ST_INDEX, a.seed);
                 my_s = (int)index_of(word(ri, lane & 3), (uint32_t)n);
             }
-            float mdx, mdy, mdz, mxi;
             if (a.proposal == QMC_CUBE) {
                 mdx = step * Rng<float>::sunif(rw.x);
                 mdy = step * Rng<float>::sunif(rw.y);
@@ -228,76 +418,24 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
             }
             mxi = logf(mxi);  // the decision is taken as 2 Delta > ln xi
             const int cnt = min(32, n - t0);
-            for (int tt = 0; tt < cnt; ++tt) {
-                const int s = __shfl_sync(FULL, my_s, tt);
-                const float dx = __shfl_sync(FULL, mdx, tt), dy = __shfl_sync(FULL, mdy, tt),
-                            dz = __shfl_sync(FULL, mdz, tt), lxi = __shfl_sync(FULL, mxi, tt);
-                const int owner = s / S, ls = s - owner * S;
-                float ax, ay, az;
-                if (owner == (int)rank) {
-                    ax = sx[ls];
-                    ay = sy[ls];
-                    az = sz[ls];
-                } else {
-                    ax = ld_cluster(map_rank(&sx[ls], (unsigned)owner));
-                    ay = ld_cluster(map_rank(&sy[ls], (unsigned)owner));
-                    az = ld_cluster(map_rank(&sz[ls], (unsigned)owner));
-                }
-                if (s == rs) {
-                    ax = rx;
-                    ay = ry;
-                    az = rz;
-                }
-                const float bx = wrap(ax + dx, L), by = wrap(ay + dy, L), bz = wrap(az + dz, L);
-                // partner terms over this slice, the moved atom masked (it adds zero)
-                const int cs = owner == (int)rank ? ls >> 2 : -1;
-                const float2 nax = make_float2(-ax, -ax), nay = make_float2(-ay, -ay), naz = make_float2(-az, -az);
-                const float2 nbx = make_float2(-bx, -bx), nby = make_float2(-by, -by), nbz = make_float2(-bz, -bz);
-                float2 acco = make_float2(0.f, 0.f), accn = make_float2(0.f, 0.f);
-                for (int c = gtid; c < nv; c += TPW) {
-                    float4 X = reinterpret_cast<const float4 *>(sx)[c];
-                    float4 Y = reinterpret_cast<const float4 *>(sy)[c];
-                    float4 Z = reinterpret_cast<const float4 *>(sz)[c];
-                    if (c == cs) {
-                        const int e = ls - 4 * c;
-                        Vec<float>::set(X, e, qnan<float>());
-                        Vec<float>::set(Y, e, qnan<float>());
-                        Vec<float>::set(Z, e, qnan<float>());
+            int tt = 0;
+            if constexpr (K > 1) {
+                for (; ok && tt + K <= cnt; tt += K) {
+                    // a batch that draws an atom twice is done one move at a time
+                    bool distinct = true;
+#pragma unroll
+                    for (int i = 0; i < K; ++i)
+#pragma unroll
+                        for (int q = i + 1; q < K; ++q)
+                            distinct &= __shfl_sync(FULL, my_s, tt + i) != __shfl_sync(FULL, my_s, tt + q);
+                    if (distinct) {
+                        ok = moves(std::integral_constant<int, K>(), tt);
+                    } else {
+                        for (int i = 0; ok && i < K; ++i) ok = moves(std::integral_constant<int, 1>(), tt + i);
                     }
-                    const float2 xa = make_float2(X.x, X.y), xb = make_float2(X.z, X.w);
-                    const float2 ya = make_float2(Y.x, Y.y), yb = make_float2(Y.z, Y.w);
-                    const float2 za = make_float2(Z.x, Z.y), zb = make_float2(Z.z, Z.w);
-                    P.acc5(__fadd2_rn(xa, nax), __fadd2_rn(ya, nay), __fadd2_rn(za, naz), acco);
-                    P.acc5(__fadd2_rn(xa, nbx), __fadd2_rn(ya, nby), __fadd2_rn(za, nbz), accn);
-                    P.acc5(__fadd2_rn(xb, nax), __fadd2_rn(yb, nay), __fadd2_rn(zb, naz), acco);
-                    P.acc5(__fadd2_rn(xb, nbx), __fadd2_rn(yb, nby), __fadd2_rn(zb, nbz), accn);
-                }
-                float delta = 0.f;
-                if (!exchange(J.c * ((accn.x + accn.y) - (acco.x + acco.y)), delta)) {
-                    ok = false;
-                    break;
-                }
-                if (delta != delta) {
-                    if (gtid == 0 && rank == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
-                    ok = false;
-                    break;
-                }
-                if (2.f * delta > lxi) {  // Eq. (Decision)
-                    if (gtid == 0 && rank == 0) lp.add(delta);
-                    ++nacc;
-                    if (owner == (int)rank && gtid == (ls >> 2) % TPW) {
-                        sx[ls] = bx;
-                        sy[ls] = by;
-                        sz[ls] = bz;
-                    }
-                    rs = s;
-                    rx = bx;
-                    ry = by;
-                    rz = bz;
-                } else {
-                    rs = -1;
                 }
             }
+            for (; ok && tt < cnt; ++tt) ok = moves(std::integral_constant<int, 1>(), tt);
         }
     }
     __syncthreads();
