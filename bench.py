@@ -190,7 +190,7 @@ def run_reference(args):
 def run_native(args):
     import torch
     import paper_1312_1282_gb300 as q
-    from paper_1312_1282_gb300 import replicas
+    from paper_1312_1282_gb300 import replicas, tuning
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -222,17 +222,7 @@ def run_native(args):
     q.qmc_log_psi(batch_descs(0.8), opt, pos, logpsi)
 
     # step tuned to ~50 % acceptance: bisection on 4-sweep probes (part of equilibration)
-    lo, hi, step = 0.1, 3.0, 0.8
-    for _ in range(5):
-        d = batch_descs(step)
-        accum.zero_()
-        q.qmc_sweep(d, opt, pos, logpsi, sweeps, seed, 4, 0, accum)
-        acc_rate = accum[:, 7].sum().item() / (W * n * 4)
-        if acc_rate > 0.5:
-            lo = step
-        else:
-            hi = step
-        step = 0.5 * (lo + hi)
+    step, _ = tuning.tune_step(batch_descs, opt, pos, logpsi, sweeps, seed, accum, target=0.5)
     d = batch_descs(step)
     if args.tpw:  # a fixed launch shape (profiling runs), else the autotuner's choice
         tpw = args.tpw
@@ -708,6 +698,7 @@ def run_c3(args):
     run would take about half an hour).  E/N of both with their errors and the combined 2 sigma."""
     import torch
     import paper_1312_1282_gb300 as q
+    from paper_1312_1282_gb300 import tuning
     torch.cuda.set_device(0)
     n, W = N_ATOMS, WALKERS
     L = qi.box_side(n, qi.RHO_HE)
@@ -728,13 +719,8 @@ def run_c3(args):
     pos, lp, sw, acc = state(q.QMC_FP32, W)
     q.qmc_init_walkers(descs(0.8, W), seed, 0.1, opt, pos)
     q.qmc_log_psi(descs(0.8, W), opt, pos, lp)
-    lo, hi, step = 0.1, 3.0, 0.8
-    for _ in range(5):  # step bisection on 4-sweep probes of the chains (as in the headline run)
-        acc.zero_()
-        q.qmc_sweep(descs(step, W), opt, pos, lp, sw, seed, 4, 0, acc)
-        rate = acc[:, 7].sum().item() / (W * n * 4)
-        lo, hi = (step, hi) if rate > 0.5 else (lo, step)
-        step = 0.5 * (lo + hi)
+    # step bisection on 4-sweep probes of the chains (as in the headline run)
+    step, _ = tuning.tune_step(lambda s: descs(s, W), opt, pos, lp, sw, seed, acc, target=0.5)
     d = descs(step, W)
     q.qmc_autotune(d, opt, pos)
     t0 = time.time()
