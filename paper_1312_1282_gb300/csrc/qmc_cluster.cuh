@@ -159,11 +159,15 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
     Jas<float, 5, true> J;
     J.init(d);
 
+    // A failure (a wait that ran out, a non-finite ratio) never changes the control flow: every
+    // thread of every CTA goes through the same exchanges and barriers to the end, where a
+    // barrier vote decides the write-back.  A thread whose wait ran out skips its later waits.
+    bool tmo = false;
     unsigned jx = 0;  // exchanges so far: slot set jx & 1, phase parity (jx >> 1) & 1
     // the sums over the cluster of K values per thread, identical in every CTA (rank order):
     // warp sums, then threads 0 .. K-1 each add one value over the warps, store it into every
     // CTA's slot and arrive on every CTA's mbarrier (release at cluster scope)
-    auto exchange = [&](float (&v)[K]) -> bool {
+    auto exchange = [&](float (&v)[K]) {
 #pragma unroll
         for (int i = 0; i < K; ++i) v[i] = warp_sum(v[i]);
         if (lane == 0)
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
                 mb_arrive_remote(map_rank(&mb[ph], (unsigned)r));
             }
         }
-        if (!mb_wait_cluster(&mb[ph], par, a.err)) return false;
+        if (!tmo && !mb_wait_cluster(&mb[ph], par, a.err)) tmo = true;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             const float *p = &part[(ph * K + i) * 8];
@@ -190,7 +194,6 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
             for (int r = 1; r < C; ++r) t += p[r];
             v[i] = t;
         }
-        return true;
     };
 
     // load this CTA's slice; entries past the walker get distinct far coordinates (1e30 scale:
@@ -215,12 +218,11 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
         float v[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) v[i] = i == 0 ? (float)bad : 0.f;
-        ok = exchange(v);
-        if (ok && v[0] != 0.f) {
-            if (gtid == 0 && rank == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
-            ok = false;
-        }
+        exchange(v);
+        if (!tmo && v[0] != 0.f && gtid == 0 && rank == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
+        ok = __syncthreads_and(!tmo && v[0] == 0.f) != 0;  // the same in every thread of the CTA
     }
+    const bool run = ok;
 
     LogPsiAcc<float> lp;
     lp.set(a.logpsi[d.slot]);
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
     float mdx = 0.f, mdy = 0.f, mdz = 0.f, mxi = 0.f;
 
     // moves tt .. tt+KK-1 of the current block (distinct atoms) with one exchange
-    auto moves = [&](auto kk_tag, int tt) -> bool {
+    auto moves = [&](auto kk_tag, int tt) {
         constexpr int KK = decltype(kk_tag)::value;
         int s[KK], own[KK], ls[KK], cs[KK];
         float ax[KK], ay[KK], az[KK], bx[KK], by[KK], bz[KK], lxi[KK];
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
 #pragma unroll
             for (int o = KK / 2; o > 0; o >>= 1) tl += __shfl_xor_sync(FULL, tl, o);
         }
-        if (!exchange(v)) return false;
+        exchange(v);
         bool acc[KK];
 #pragma unroll
         for (int i = 0; i < KK; ++i) {
@@ -362,9 +364,9 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
                     if (acc[k]) delta += dik;
                 }
             }
-            if (delta != delta) {
+            if (delta != delta) {  // flagged; the move is rejected and the sweep goes on
                 if (gtid == 0 && rank == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
-                return false;
+                ok = false;
             }
             acc[i] = 2.f * delta > lxi[i];  // Eq. (Decision)
             if (acc[i]) {
@@ -386,12 +388,11 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
         }
 #pragma unroll
         for (int q = KK; q < K; ++q) ps[q] = -1;
-        return true;
     };
 
-    for (int it = 0; ok && it < a.nsweeps; ++it) {
+    for (int it = 0; run && it < a.nsweeps; ++it) {
         const uint32_t k = (uint32_t)(k0 + (unsigned long long)it);
-        for (int t0 = 0; ok && t0 < n; t0 += 32) {
+        for (int t0 = 0; t0 < n; t0 += 32) {
             // random numbers of moves t0 .. t0+31, one move per lane, as in the one-CTA sweep
             const uint32_t t = (uint32_t)(t0 + lane);
             const uint4 rw = philox(t, k, d.wid, ST_STEP, a.seed);
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
             const int cnt = min(32, n - t0);
             int tt = 0;
             if constexpr (K > 1) {
-                for (; ok && tt + K <= cnt; tt += K) {
+                for (; tt + K <= cnt; tt += K) {
                     // a batch that draws an atom twice is done one move at a time
                     bool distinct = true;
 #pragma unroll
@@ -429,17 +430,17 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
                         for (int q = i + 1; q < K; ++q)
                             distinct &= __shfl_sync(FULL, my_s, tt + i) != __shfl_sync(FULL, my_s, tt + q);
                     if (distinct) {
-                        ok = moves(std::integral_constant<int, K>(), tt);
+                        moves(std::integral_constant<int, K>(), tt);
                     } else {
-                        for (int i = 0; ok && i < K; ++i) ok = moves(std::integral_constant<int, 1>(), tt + i);
+                        for (int i = 0; i < K; ++i) moves(std::integral_constant<int, 1>(), tt + i);
                     }
                 }
             }
-            for (; ok && tt < cnt; ++tt) ok = moves(std::integral_constant<int, 1>(), tt);
+            for (; tt < cnt; ++tt) moves(std::integral_constant<int, 1>(), tt);
         }
     }
-    __syncthreads();
-    if (ok) {  // write back (every CTA its slice; rank 0 the walker's scalars)
+    // write back (every CTA its slice; rank 0 the walker's scalars) unless a thread failed
+    if (__syncthreads_and(ok && !tmo)) {
         for (int i = gtid; i < ns; i += TPW) {
             gx[j0 + i] = sx[i];
             gx[d.pad + j0 + i] = sy[i];
