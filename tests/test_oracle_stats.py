@@ -66,6 +66,46 @@ def test_two_particles_match_exact_integrals():
     assert 0.05 < acc < 0.95
 
 
+def test_two_particle_distance_density_matches_exact():
+    """The sampled minimum-image pair distance of N = 2 has density 4 pi r^2 exp(2 u(r)) / Z below
+    L/2, and the corners of the cube (u = 0) take the rest: 16 bins of 0.25 A plus the corners,
+    frequencies over 40 blocks of thinned samples, every bin within 5 standard errors and a
+    chi^2 with the block variances within its spread."""
+    L, b = 8.0, 3.07
+    h = L / 2
+    nb = 16
+    w = lambda r: 4 * math.pi * r * r * math.exp(2 * oracle.pair_u(r, L, b)[0])  # noqa: E731
+    corners = L ** 3 - 4 * math.pi / 3 * h ** 3
+    edges = np.linspace(0.0, h, nb + 1)
+    inner = [quad(w, edges[i], edges[i + 1], limit=200)[0] for i in range(nb)]
+    Z = sum(inner) + corners
+    want = np.array(inner + [corners]) / Z
+    assert abs(want.sum() - 1.0) < 1e-12
+
+    P = oracle.make_walker(2, L, b, step=2.0, seed=0xD15, wid=0)
+    pos = np.array([[1.0, 5.0], [1.0, 5.0], [1.0, 5.0]])
+    lp = oracle.log_psi(pos, L, b)
+    pos, lp, k, _, _ = oracle.run_walker(P, pos, lp, 0, 100, 0)  # burn-in
+    nblocks, per_block = 40, 500
+    frac = np.zeros((nblocks, nb + 1))
+    for blk in range(nblocks):
+        for _ in range(per_block):
+            pos, lp, k, _, _ = oracle.run_walker(P, pos, lp, k, 2, 0)
+            d = pos[:, 0] - pos[:, 1]
+            d -= L * np.round(d / L)
+            r = math.sqrt(float(d @ d))
+            frac[blk, min(int(r / h * nb), nb) if r < h else nb] += 1.0 / per_block
+    mean = frac.mean(0)
+    se = frac.std(0, ddof=1) / math.sqrt(nblocks)
+    assert np.all(np.abs(mean - want) < 5 * se + 5e-4), np.c_[mean, want, se]
+    live = se > 0
+    chi2 = float((((mean - want) / np.where(live, se, 1.0)) ** 2)[live].sum())
+    dof = int(live.sum())
+    assert chi2 < dof + 6 * math.sqrt(2 * dof), (chi2, dof)
+    # the contact region is excluded: no sample below 2 A (exp(2u) < 1e-3 there)
+    assert mean[:8].sum() < 1e-3
+
+
 def test_no_correlation_limit_accepts_every_move():
     L = 8.0
     P = oracle.make_walker(2, L, 0.0, step=2.0, seed=3, wid=0)
