@@ -39,8 +39,9 @@ METRIC = "pair evals/s and sweeps/s at N=1952, FP32-batched vs FP64 plain, E/ato
 WORKLOAD = "VMC liquid 4He N=1952 rho=0.02186 b=3.07 m=5 Aziz-II, 528 walkers, 5 sweeps + 1 local energy per step"
 # FP32 operations per pair evaluation of a move (difference 3, image fold 6, r^2 3, clamp 1,
 # r and L - r 2, q^2 q^4 w^2 w^4 4, two fused multiply-accumulates 2) and per unordered pair of
-# the local-energy pass (71); the op lists are in the design doc.  SFU operations (2 and 3-4) are not
-# counted.
+# the local-energy pass (difference 3, signed image 12, r^2 3, mask 1, f, f', f'' 9, the f(L - r)
+# terms 10, drift and its row/column sums 10, Laplacian term 3, Aziz II 16: 71).  SFU operations
+# (2 and 3-4) are not counted.
 C_PAIR = 21.0
 C_ENERGY = 71.0
 FP32_LANES_PER_SM = 128
@@ -217,7 +218,7 @@ def run_native(args):
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     logpsi = torch.zeros(W, dtype=torch.float64, device="cuda")
     sweeps = torch.zeros(W, dtype=torch.int64, device="cuda")
-    accum = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+    accum = torch.zeros(W, q.NACC, dtype=torch.float64, device="cuda")
     q.qmc_init_walkers(batch_descs(0.8), seed, 0.1, opt, pos)
     q.qmc_log_psi(batch_descs(0.8), opt, pos, logpsi)
 
@@ -225,10 +226,10 @@ def run_native(args):
     step, _ = tuning.tune_step(batch_descs, opt, pos, logpsi, sweeps, seed, accum, target=0.5)
     d = batch_descs(step)
     if args.tpw:  # a fixed launch shape (profiling runs), else the autotuner's choice
-        tpw = args.tpw
-        opt = q.options(precision=q.QMC_FP32, recompute_every=50, threads_per_walker=tpw)
+        tpw, groups = args.tpw, max(1, args.groups)
+        opt = q.options(precision=q.QMC_FP32, recompute_every=50, threads_per_walker=tpw, walkers_per_cta=groups)
     else:
-        tpw = q.qmc_autotune(d, opt, pos)
+        tpw, groups = q.qmc_autotune(d, opt, pos)
     q.qmc_sweep(d, opt, pos, logpsi, sweeps, seed, args.equil, 0, accum)
     accum.zero_()
     torch.cuda.synchronize()
@@ -280,7 +281,7 @@ def run_native(args):
     pos64 = pos[:3 * pad].double().contiguous()
     lp64, sw64, acc64 = torch.zeros(1, dtype=torch.float64, device="cuda"), torch.zeros(1, dtype=torch.int64,
                                                                                          device="cuda"), \
-        torch.zeros(1, 8, dtype=torch.float64, device="cuda")
+        torch.zeros(1, q.NACC, dtype=torch.float64, device="cuda")
     q.qmc_sweep(d1, opt64, pos64, lp64, sw64, seed, 1, 0, acc64)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -292,7 +293,7 @@ def run_native(args):
     # ---- end to end through the public API, host buffers (pinned) ----
     host_pos = pos.cpu().pin_memory()
     host_lp, host_sw = logpsi.cpu().pin_memory(), sweeps.cpu().pin_memory()
-    host_acc = torch.zeros(W, 8, dtype=torch.float64).pin_memory()
+    host_acc = torch.zeros(W, q.NACC, dtype=torch.float64).pin_memory()
     out_pos, out_acc = torch.empty_like(host_pos).pin_memory(), torch.empty_like(host_acc).pin_memory()
     e2e_steps = max(3, min(args.steps, 10))
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -318,8 +319,8 @@ def run_native(args):
     x1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = x0.elapsed_time(x1) / e2e_steps
-    h2d = host_pos.numel() * 4 + W * 8 * 10
-    d2h = out_pos.numel() * 4 + W * 8 * 8
+    h2d = host_pos.numel() * 4 + W * 8 * (2 + q.NACC)  # positions, ln psi, sweep counters, sums
+    d2h = out_pos.numel() * 4 + W * 8 * q.NACC  # positions and sums
     # the copies alone, for the breakdown of the end-to-end step
     x0.record(stream)
     for _ in range(e2e_steps):
@@ -370,6 +371,7 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_atoms": n, "walkers_per_gpu": W, "sweeps_per_step": SWEEPS_PER_STEP,
                        "energy_every": SWEEPS_PER_STEP, "step_A": round(step, 4), "threads_per_walker": tpw,
+                       "walkers_per_cta": groups,
                        "sms": nsm, "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas{world}"},
             "sweeps_per_s": sweeps_per_s,
             "energy_pairs_per_s": energy_pairs * world * args.steps / (total_ms * 1e-3),
@@ -429,14 +431,14 @@ def run_uneven(args):
     pos = torch.empty(off, dtype=torch.float32, device="cuda")
     lp = torch.zeros(W, dtype=torch.float64, device="cuda")
     sw = torch.zeros(W, dtype=torch.int64, device="cuda")
-    acc = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+    acc = torch.zeros(W, q.NACC, dtype=torch.float64, device="cuda")
     q.qmc_init_walkers(d, 0x5EED0004, 0.1, opt, pos)
     q.qmc_log_psi(d, opt, pos, lp)
     if args.tpw:
-        tpw = args.tpw
-        opt = q.options(precision=q.QMC_FP32, recompute_every=50, threads_per_walker=tpw)
+        tpw, groups = args.tpw, max(1, args.groups)
+        opt = q.options(precision=q.QMC_FP32, recompute_every=50, threads_per_walker=tpw, walkers_per_cta=groups)
     else:
-        tpw = q.qmc_autotune(d, opt, pos)
+        tpw, groups = q.qmc_autotune(d, opt, pos)
     q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0004, args.equil, 0, acc)
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()
@@ -466,7 +468,8 @@ def run_uneven(args):
     for r, row in zip(a_np, rows):
         groups.setdefault(row[0], []).append(r[0] / r[6] / row[0])
     print(json.dumps({"config": "uneven batch, one persistent launch per step, CUDA graph replay",
-                      "walkers": W, "threads_per_walker": tpw, "ms_per_step": ms, "pair_evals_per_s": pe / (ms * 1e-3),
+                      "walkers": W, "threads_per_walker": tpw, "walkers_per_cta": groups, "ms_per_step": ms,
+                      "pair_evals_per_s": pe / (ms * 1e-3),
                       "E_per_atom_by_N": {str(k): float(np.mean(v)) for k, v in sorted(groups.items())}}), flush=True)
     return 0
 
@@ -491,11 +494,11 @@ def run_large(args):
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     lp = torch.zeros(W, dtype=torch.float64, device="cuda")
     sw = torch.zeros(W, dtype=torch.int64, device="cuda")
-    acc = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+    acc = torch.zeros(W, q.NACC, dtype=torch.float64, device="cuda")
     grad = torch.zeros(W, 6, dtype=torch.float64, device="cuda")
     q.qmc_init_walkers(d, 0x5EED0005, 0.1, opt, pos)
     q.qmc_log_psi(d, opt, pos, lp)
-    tpw = q.qmc_autotune(d, opt, pos)
+    tpw, _ = q.qmc_autotune(d, opt, pos)
     q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, args.equil, 0, acc)
     acc.zero_()
     for _ in range(args.warmup):
@@ -551,7 +554,7 @@ def run_fp64cmp(args):
         pos = torch.empty(W * 3 * pad, dtype=dt, device="cuda")
         lp = torch.zeros(W, dtype=torch.float64, device="cuda")
         sw = torch.zeros(W, dtype=torch.int64, device="cuda")
-        acc = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+        acc = torch.zeros(W, q.NACC, dtype=torch.float64, device="cuda")
         q.qmc_init_walkers(d, 0x5EED0002, 0.1, opt, pos)
         q.qmc_log_psi(d, opt, pos, lp)
         q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0002, 500, 0, acc)
@@ -608,11 +611,11 @@ def run_t2e(args):
         pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
         lp = torch.zeros(W, dtype=torch.float64, device="cuda")
         sw = torch.zeros(W, dtype=torch.int64, device="cuda")
-        acc = torch.zeros(W, 8, dtype=torch.float64, device="cuda")
+        acc = torch.zeros(W, q.NACC, dtype=torch.float64, device="cuda")
         seed = 0x5EED0006 + n
         q.qmc_init_walkers(d, seed, 0.1, opt, pos)
         q.qmc_log_psi(d, opt, pos, lp)
-        tpw_sweep = q.qmc_autotune(d, opt, pos)
+        tpw_sweep, _ = q.qmc_autotune(d, opt, pos)
         q.qmc_sweep(d, opt, pos, lp, sw, seed, 300, 0, acc)
         torch.cuda.synchronize()
 
@@ -713,7 +716,7 @@ def run_c3(args):
         return (torch.empty(walkers * 3 * pad, dtype=dt, device="cuda"),
                 torch.zeros(walkers, dtype=torch.float64, device="cuda"),
                 torch.zeros(walkers, dtype=torch.int64, device="cuda"),
-                torch.zeros(walkers, 8, dtype=torch.float64, device="cuda"))
+                torch.zeros(walkers, q.NACC, dtype=torch.float64, device="cuda"))
 
     opt = q.options(precision=q.QMC_FP32, recompute_every=50)
     pos, lp, sw, acc = state(q.QMC_FP32, W)
@@ -789,6 +792,7 @@ def main():
     ap.add_argument("--equil", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--tpw", type=int, default=0, help="threads per walker of the headline run (0: autotune)")
+    ap.add_argument("--groups", type=int, default=0, help="walkers per CTA with --tpw (default 1)")
     ap.add_argument("--large-n", type=int, default=10000, help="large: atoms per walker")
     ap.add_argument("--c3-fp64-sweeps", type=int, default=600, help="c3: measured FP64 sweeps")
     ap.add_argument("--large-sweeps", type=int, default=20, help="large: sweeps per step")

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define QMC_VERSION 100 /* 1.0.0 */
+#define QMC_VERSION 110 /* 1.1.0 */
 
 #define QMC_OK 0
 #define QMC_ERR_ARG (-1)      /* null pointer, W <= 0, n < 2, bad padding/alignment, non-finite or
@@ -58,7 +58,16 @@ extern "C" {
 #define QMC_DEVERR_NONFINITE_POS 1u   /* a loaded coordinate was NaN/Inf or outside [0, L] */
 #define QMC_DEVERR_NONFINITE_RATIO 2u /* a trial log-ratio was NaN */
 #define QMC_DEVERR_BAD_INDEX 4u       /* qmc_trial_delta: an atom index outside [0, n) (move skipped) */
-#define QMC_DEVERR_TIMEOUT 8u         /* qmc_sweep: a wait on the walker queue exceeded 10 s */
+#define QMC_DEVERR_TIMEOUT 8u         /* qmc_sweep: a wait on the walker queue or on a cluster
+                                         exchange exceeded its limit (10 s) */
+
+/* Per-walker accumulator record of qmc_sweep: QMC_ACCUM_FIELDS doubles per walker, W-major.
+ *   0 sum E_L   1 sum E_L^2   2 sum V   3 sum T_L   4 sum T_PB   5 sum T_F   (energy samples)
+ *   6 number of energy samples            7 number of accepted moves
+ *   8 sum over ln psi recomputes of |ln psi carried - ln psi recomputed|   (the drift of the
+ *     incrementally updated ln psi of Eq. (JastrowUpdate) against Eq. (Jastrow))
+ *   9 largest such |drift| (a maximum, not a sum; starts from the value passed in) */
+#define QMC_ACCUM_FIELDS 10
 
 /* One walker (one Markov chain).  64 bytes. */
 typedef struct qmc_walker_desc {
@@ -73,7 +82,7 @@ typedef struct qmc_walker_desc {
     double step;    /* trial step: cube half-width (QMC_CUBE) or sigma (QMC_GAUSS), Angstrom */
 } qmc_walker_desc;
 
-/* Options shared by a call.  32 bytes. */
+/* Options shared by a call.  40 bytes. */
 typedef struct qmc_options {
     int32_t precision;          /* QMC_FP32 or QMC_FP64 */
     int32_t proposal;           /* QMC_CUBE or QMC_GAUSS */
@@ -85,6 +94,10 @@ typedef struct qmc_options {
                                    (k+1) % recompute_every == 0; 0 = never */
     int32_t threads_per_walker; /* 0 = autotuned choice (or built-in heuristic); else one of
                                    32, 64, 128, 256, 512, 1024 */
+    int32_t walkers_per_cta;    /* 0 = autotuned choice (or built-in heuristic); else 1..8 walkers
+                                   share one CTA (walkers_per_cta * threads_per_walker <= 256, or
+                                   1); ignored where a walker is served by a whole CTA or more */
+    int32_t reserved;           /* must be 0 */
 } qmc_options;
 
 /*
@@ -111,8 +124,8 @@ int qmc_init_walkers(const qmc_walker_desc *d, int W, uint64_t seed, double jitt
  *   pos      in/out device positions
  *   logpsi   in/out [W] device, running ln psi (only carried, never used for decisions)
  *   sweep    in/out [W] device, uint64 absolute sweep index k of each walker's next sweep
- *   accum    in/out [W*8] device, added to: {sum E_L, sum E_L^2, sum V, sum T_L, sum T_PB,
- *            sum T_F, number of samples, number of accepted moves}
+ *   accum    in/out [W*QMC_ACCUM_FIELDS] device, added to: the energy sums, sample and
+ *            acceptance counts and the ln psi drift of each recompute (see QMC_ACCUM_FIELDS)
  * The same (seed, id, k) always reproduces the same chain: a run split over several calls is
  * bit-identical to one call.
  * Device memory: the first call of a batch allocates its walker table (and, for batches of
@@ -175,13 +188,18 @@ int qmc_pair_hist(const qmc_walker_desc *d, int W, const qmc_options *opt, const
                   double rmax, uint64_t *hist, void *stream);
 
 /*
- * qmc_autotune -- time qmc_sweep on a scratch copy of `pos` for each admissible
- * threads-per-walker choice and remember the fastest for batches of this shape (largest n,
- * W, precision, exponent); later calls with threads_per_walker = 0 use it.  Synchronises the
- * stream.  *tpw_out (may be NULL) receives the choice.
+ * qmc_autotune -- the launch shape of qmc_sweep chosen by measurement (the paper's heuristics of
+ * Sec. 4.3 -- as many resident blocks as fit, fewer threads than atoms, multiples of 32 -- are
+ * the search space): qmc_sweep is timed on a scratch copy of `pos` for every admissible pair
+ * (threads per walker, walkers per CTA) -- threads 32 .. 1024 in powers of two, at most one
+ * thread per 4-atom partner chunk; walkers per CTA 1, 2, 4, 8 with at most 256 threads and the
+ * shared memory of one CTA -- and the fastest pair is remembered for batches of this shape
+ * (largest n, W, precision, exponent, proposal).  Later calls whose options leave
+ * threads_per_walker or walkers_per_cta at 0 use it.  Synchronises the stream.
+ *   tpw_out, groups_out   (may be NULL) receive the chosen threads per walker and walkers per CTA.
  */
 int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos,
-                 void *stream, int *tpw_out);
+                 void *stream, int *tpw_out, int *groups_out);
 
 /*
  * qmc_sweep_static -- qmc_sweep for callers that cannot allocate device memory.
@@ -197,14 +215,17 @@ int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const 
  *   Arguments and results are those of qmc_sweep, plus
  *   err      optional device uint32 that receives QMC_DEVERR_* bits of this call (OR-ed into
  *            it); if NULL the bits go to a word in the fixed array, which is cleared at the
- *            start of every call and cannot be read back.
+ *            start of every call and which qmc_status() reads and clears with its own word.
  *   W        at most QMC_STATIC_MAX_WALKERS; larger batches are rejected with QMC_ERR_ARG.
  * The first call on a device looks up the fixed array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  Every call overwrites the whole array:
  * calls whose work overlaps on the GPU (on different streams without ordering) race on it and
  * must not be issued.  Calls on one stream are ordered and safe.  The descriptors are copied
  * from host memory with cudaMemcpyAsync from a staging area inside the library, so two host
- * threads calling at once are serialised while they enqueue.
+ * threads calling at once are serialised while they enqueue.  Because that staging area is
+ * reused by the next call, a call made while `stream` is being captured is refused with
+ * QMC_ERR_ARG before anything is enqueued (a recorded copy would read whatever the latest
+ * call staged when the graph is replayed).
  */
 #define QMC_STATIC_MAX_WALKERS 4096
 #define QMC_STATIC_SCRATCH_BYTES (QMC_STATIC_MAX_WALKERS * 76 + 256)
@@ -217,7 +238,8 @@ int qmc_capacity(int precision);
 
 /*
  * qmc_status -- wait for `stream` (at most timeout_ms, <= 0 means no limit), then read and clear
- * the device error word.  Returns QMC_OK, QMC_ERR_DEVICE (bits in *bits if non-NULL),
+ * the device error word of the current device (and the word that qmc_sweep_static uses when it
+ * is given no `err`).  Returns QMC_OK, QMC_ERR_DEVICE (bits in *bits if non-NULL),
  * QMC_ERR_TIMEOUT or QMC_ERR_CUDA.
  */
 int qmc_status(void *stream, int timeout_ms, uint32_t *bits);

@@ -23,13 +23,15 @@ __all__ = [
     "QMC_FP32", "QMC_FP64", "QMC_CUBE", "QMC_GAUSS", "QmcError", "WalkerDesc", "Options", "lib", "descs",
     "options", "qmc_init_walkers", "qmc_sweep", "qmc_local_energy", "qmc_energy_grad", "qmc_log_psi",
     "qmc_trial_delta", "qmc_pair_hist", "pair_correlation", "qmc_sweep_static", "QMC_STATIC_MAX_WALKERS", "qmc_autotune", "qmc_capacity", "qmc_status", "qmc_launch_count", "qmc_version",
-    "qmc_shutdown", "Batch", "QmcGrad", "ACCUM_FIELDS", "ENERGY_FIELDS", "GRAD_FIELDS",
+    "qmc_shutdown", "Batch", "QmcGrad", "ACCUM_FIELDS", "NACC", "ENERGY_FIELDS", "GRAD_FIELDS",
 ]
 
 QMC_FP32, QMC_FP64 = 0, 1
 QMC_CUBE, QMC_GAUSS = 0, 1
 QMC_STATIC_MAX_WALKERS = 4096
-ACCUM_FIELDS = ("sum_EL", "sum_EL2", "sum_V", "sum_TL", "sum_TPB", "sum_TF", "samples", "accepted")
+ACCUM_FIELDS = ("sum_EL", "sum_EL2", "sum_V", "sum_TL", "sum_TPB", "sum_TF", "samples", "accepted",
+                "sum_logpsi_drift", "max_logpsi_drift")
+NACC = len(ACCUM_FIELDS)  # QMC_ACCUM_FIELDS: doubles per walker in the accumulator record
 ENERGY_FIELDS = ("V", "T_L", "T_PB", "T_F", "E_L")
 GRAD_FIELDS = ("logpsi", "E_L", "dlogpsi_db", "dlogpsi_dm", "dEL_db", "dEL_dm")
 _ERRORS = {-1: "QMC_ERR_ARG", -2: "QMC_ERR_CAPACITY", -3: "QMC_ERR_CUDA", -4: "QMC_ERR_DEVICE", -5: "QMC_ERR_TIMEOUT"}
@@ -50,13 +52,14 @@ class WalkerDesc(C.Structure):
 
 
 class Options(C.Structure):
-    """qmc_options (32 bytes)."""
+    """qmc_options (40 bytes)."""
 
     _fields_ = [("precision", C.c_int32), ("proposal", C.c_int32), ("sym", C.c_int32), ("sequential", C.c_int32),
-                ("hbar2_over_m", C.c_double), ("recompute_every", C.c_int32), ("threads_per_walker", C.c_int32)]
+                ("hbar2_over_m", C.c_double), ("recompute_every", C.c_int32), ("threads_per_walker", C.c_int32),
+                ("walkers_per_cta", C.c_int32), ("reserved", C.c_int32)]
 
 
-assert C.sizeof(WalkerDesc) == 64 and C.sizeof(Options) == 32
+assert C.sizeof(WalkerDesc) == 64 and C.sizeof(Options) == 40
 
 _lib = None
 _VP, _DP = C.c_void_p, C.POINTER(C.c_double)
@@ -77,7 +80,7 @@ def lib():
         L.qmc_energy_grad.argtypes = [D, C.c_int, O, _VP, _VP, _VP]
         L.qmc_log_psi.argtypes = [D, C.c_int, O, _VP, _VP, _VP]
         L.qmc_trial_delta.argtypes = [D, C.c_int, O, _VP, _VP, _VP, C.c_int, _VP, _VP]
-        L.qmc_autotune.argtypes = [D, C.c_int, O, _VP, _VP, C.POINTER(C.c_int)]
+        L.qmc_autotune.argtypes = [D, C.c_int, O, _VP, _VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.qmc_pair_hist.argtypes = [D, C.c_int, O, _VP, C.c_int, C.c_double, _VP, _VP]
         L.qmc_sweep_static.argtypes = [D, C.c_int, O, _VP, _VP, _VP, C.c_uint64, C.c_int, C.c_int, _VP, _VP, _VP]
         L.qmc_capacity.argtypes = [C.c_int]
@@ -129,8 +132,9 @@ def descs(rows) -> C.Array:
 
 
 def options(precision=QMC_FP32, proposal=QMC_CUBE, sym=1, sequential=0, hbar2_over_m=12.1194, recompute_every=50,
-            threads_per_walker=0) -> Options:
-    return Options(precision, proposal, sym, sequential, hbar2_over_m, recompute_every, threads_per_walker)
+            threads_per_walker=0, walkers_per_cta=0) -> Options:
+    return Options(precision, proposal, sym, sequential, hbar2_over_m, recompute_every, threads_per_walker,
+                   walkers_per_cta, 0)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -213,10 +217,11 @@ def pair_correlation(counts, n, L, rmax, samples):
 
 
 @_traced
-def qmc_autotune(d, opt, pos, stream=None) -> int:
-    t = C.c_int(0)
-    _check(lib().qmc_autotune(d, len(d), C.byref(opt), _ptr(pos), _stream(stream), C.byref(t)))
-    return t.value
+def qmc_autotune(d, opt, pos, stream=None) -> tuple[int, int]:
+    """The measured launch shape of qmc_sweep for this batch: (threads per walker, walkers per CTA)."""
+    t, g = C.c_int(0), C.c_int(0)
+    _check(lib().qmc_autotune(d, len(d), C.byref(opt), _ptr(pos), _stream(stream), C.byref(t), C.byref(g)))
+    return t.value, g.value
 
 
 def qmc_capacity(precision) -> int:
@@ -272,7 +277,7 @@ class Batch:
         self.pos = torch.zeros(off, dtype=dt, device=self.device)
         self.logpsi = torch.zeros(self.W, dtype=torch.float64, device=self.device)
         self.sweeps = torch.zeros(self.W, dtype=torch.int64, device=self.device)
-        self.accum = torch.zeros(self.W, 8, dtype=torch.float64, device=self.device)
+        self.accum = torch.zeros(self.W, NACC, dtype=torch.float64, device=self.device)
         self.seed = 0
 
     @property

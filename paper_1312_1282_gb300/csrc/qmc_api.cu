@@ -62,6 +62,10 @@ struct DeviceState {
 std::mutex g_mu;
 DeviceState g_dev[MAX_DEVICES];
 
+// device address of the error word of qmc_sweep_static on device `dev` (nullptr until that entry
+// point has run there); defined with the static scratch at the end of this file
+unsigned *static_error_word(int dev);
+
 struct Plan {
     int device = 0;
     uint64_t key = 0;
@@ -77,8 +81,37 @@ struct Plan {
     bool m5 = true;
 };
 
-std::list<Plan *> g_plans;                 // most recently used first
-std::unordered_map<uint64_t, int> g_tuned;  // shape key -> threads per walker
+struct Tuned {
+    int tpw, G;  // threads per walker, walkers per CTA
+};
+std::list<Plan *> g_plans;                    // most recently used first
+std::unordered_map<uint64_t, Tuned> g_tuned;  // shape key -> autotuned launch shape
+
+// Failure tests only (the library's own tests run them in child processes): QMC_WAIT_LIMIT_MS
+// shortens the limit of every bounded device wait (default 10 s); QMC_TEST_DROP=queue makes the
+// persistent sweep never push back the first walker of its order after its first chunk, and
+// QMC_TEST_DROP=cluster makes CTA rank 1 of the first walker's cluster never take part in an
+// exchange -- so that waits run out and QMC_DEVERR_TIMEOUT is raised without any fault.
+struct TestKnobs {
+    unsigned long long wait_ns = 10000000000ull;
+    int drop_queue = 0, drop_cluster = 0;
+};
+const TestKnobs &knobs()
+{
+    static const TestKnobs k = [] {
+        TestKnobs t;
+        if (const char *e = std::getenv("QMC_WAIT_LIMIT_MS")) {
+            const long long ms = std::atoll(e);
+            if (ms > 0 && ms < 10000) t.wait_ns = (unsigned long long)ms * 1000000ull;
+        }
+        if (const char *e = std::getenv("QMC_TEST_DROP")) {
+            t.drop_queue = std::strcmp(e, "queue") == 0;
+            t.drop_cluster = std::strcmp(e, "cluster") == 0;
+        }
+        return t;
+    }();
+    return k;
+}
 
 uint64_t fnv(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
 {
@@ -132,6 +165,10 @@ int check_options(const qmc_options *o)
     const int t = o->threads_per_walker;
     if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256 && t != 512 && t != 1024)
         return fail(QMC_ERR_ARG, "threads_per_walker must be 0 or a power of two in 32..1024");
+    const int g = o->walkers_per_cta;
+    if (g < 0 || g > 8) return fail(QMC_ERR_ARG, "walkers_per_cta must be in 0..8");
+    if (g > 1 && t != 0 && g * t > 256) return fail(QMC_ERR_ARG, "walkers_per_cta x threads_per_walker exceeds 256");
+    if (o->reserved != 0) return fail(QMC_ERR_ARG, "options.reserved must be 0");
     return QMC_OK;
 }
 
@@ -197,6 +234,39 @@ int sites_of(int n)
     return 4 * nc * nc * nc;
 }
 
+// Validate one descriptor into a device-table entry.  Used by resolve() (qmc_sweep and the
+// passes) and by qmc_sweep_static, which has no containers to fill.
+int resolve_one(const qmc_walker_desc &x, int w, const qmc_options *o, DevWalker &v)
+{
+    if (x.n < 2) return fail(QMC_ERR_ARG, "walker %d: n = %d < 2", w, x.n);
+    if (x.pad_n < x.n || x.pad_n % 4) return fail(QMC_ERR_ARG, "walker %d: pad_n must be >= n and a multiple of 4", w);
+    if (x.offset < 0 || x.offset % 4) return fail(QMC_ERR_ARG, "walker %d: offset must be >= 0 and a multiple of 4", w);
+    double L = x.L;
+    if (!(L > 0)) {
+        if (!is_fin(x.rho) || x.rho <= 0) return fail(QMC_ERR_ARG, "walker %d: need L > 0 or rho > 0", w);
+        L = std::cbrt((double)x.n / x.rho);
+    }
+    if (!is_fin(L)) return fail(QMC_ERR_ARG, "walker %d: non-finite box side", w);
+    if (!is_fin(x.b) || x.b < 0) return fail(QMC_ERR_ARG, "walker %d: b must be finite and >= 0", w);
+    if (!is_fin(x.m_exp) || x.m_exp <= 0) return fail(QMC_ERR_ARG, "walker %d: m_exp must be finite and > 0", w);
+    if (!is_fin(x.step) || x.step <= 0) return fail(QMC_ERR_ARG, "walker %d: step must be finite and > 0", w);
+    // a displacement must stay below one box length so one fold puts it back into the box
+    const double reach = o->proposal == QMC_CUBE ? x.step : 6.8 * x.step;
+    if (reach >= L) return fail(QMC_ERR_ARG, "walker %d: step too large for box side %g", w, L);
+    v.n = x.n;
+    v.pad = x.pad_n;
+    v.off = x.offset;
+    v.wid = (uint32_t)x.id;
+    v.slot = w;
+    v.L = L;
+    v.b = x.b;
+    v.m = x.m_exp;
+    v.step = x.step;
+    v.c = -0.5 * std::pow(x.b, x.m_exp);
+    v.K = o->sym ? 2.0 * v.c * std::pow(2.0 / L, x.m_exp) : 0.0;
+    return QMC_OK;
+}
+
 // Validate and resolve descriptors (host copy of the device table).
 int resolve(const qmc_walker_desc *d, int W, const qmc_options *o, Plan &P, std::vector<DevWalker> &out,
             std::vector<int> &order)
@@ -206,33 +276,8 @@ int resolve(const qmc_walker_desc *d, int W, const qmc_options *o, Plan &P, std:
     P.m5 = true;
     for (int w = 0; w < W; ++w) {
         const qmc_walker_desc &x = d[w];
-        if (x.n < 2) return fail(QMC_ERR_ARG, "walker %d: n = %d < 2", w, x.n);
-        if (x.pad_n < x.n || x.pad_n % 4) return fail(QMC_ERR_ARG, "walker %d: pad_n must be >= n and a multiple of 4", w);
-        if (x.offset < 0 || x.offset % 4) return fail(QMC_ERR_ARG, "walker %d: offset must be >= 0 and a multiple of 4", w);
-        double L = x.L;
-        if (!(L > 0)) {
-            if (!is_fin(x.rho) || x.rho <= 0) return fail(QMC_ERR_ARG, "walker %d: need L > 0 or rho > 0", w);
-            L = std::cbrt((double)x.n / x.rho);
-        }
-        if (!is_fin(L)) return fail(QMC_ERR_ARG, "walker %d: non-finite box side", w);
-        if (!is_fin(x.b) || x.b < 0) return fail(QMC_ERR_ARG, "walker %d: b must be finite and >= 0", w);
-        if (!is_fin(x.m_exp) || x.m_exp <= 0) return fail(QMC_ERR_ARG, "walker %d: m_exp must be finite and > 0", w);
-        if (!is_fin(x.step) || x.step <= 0) return fail(QMC_ERR_ARG, "walker %d: step must be finite and > 0", w);
-        // a displacement must stay below one box length so one fold puts it back into the box
-        const double reach = o->proposal == QMC_CUBE ? x.step : 6.8 * x.step;
-        if (reach >= L) return fail(QMC_ERR_ARG, "walker %d: step too large for box side %g", w, L);
-        DevWalker &v = out[w];
-        v.n = x.n;
-        v.pad = x.pad_n;
-        v.off = x.offset;
-        v.wid = (uint32_t)x.id;
-        v.slot = w;
-        v.L = L;
-        v.b = x.b;
-        v.m = x.m_exp;
-        v.step = x.step;
-        v.c = -0.5 * std::pow(x.b, x.m_exp);
-        v.K = o->sym ? 2.0 * v.c * std::pow(2.0 / L, x.m_exp) : 0.0;
+        const int rc = resolve_one(x, w, o, out[w]);
+        if (rc) return rc;
         P.maxn = std::max(P.maxn, x.n);
         P.maxpad = std::max(P.maxpad, x.pad_n);
         P.maxsites = std::max(P.maxsites, sites_of(x.n));
@@ -329,16 +374,23 @@ int pow2_at_least(int x)
     return p;
 }
 
+// the autotuned launch shape of this batch shape, if any
+bool tuned_shape(const Plan &P, const qmc_options *o, int dev, Tuned &t)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_tuned.find(shape_key(dev, P, o));
+    if (it == g_tuned.end()) return false;
+    t = it->second;
+    return true;
+}
+
 // Threads per walker: explicit option, then the autotuned choice, then a heuristic aiming at
 // ~16 resident warps per SM while every thread keeps at least one 4-atom partner chunk.
 int choose_tpw(const Plan &P, const qmc_options *o, int dev, int nsm)
 {
     if (o->threads_per_walker) return o->threads_per_walker;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        auto it = g_tuned.find(shape_key(dev, P, o));
-        if (it != g_tuned.end()) return it->second;
-    }
+    Tuned tu;
+    if (tuned_shape(P, o, dev, tu)) return tu.tpw;
     const int chunks = (P.maxn + 3) / 4;
     int t = pow2_at_least((int)std::ceil(512.0 * nsm / P.W));
     t = std::min(t, pow2_at_least(chunks));
@@ -361,16 +413,33 @@ int drift_scratch(DeviceState *ds, size_t need, float **out)
     return QMC_OK;
 }
 
-// Walkers per CTA: one, unless the batch has so many small walkers that the 32-CTA-per-SM
-// limit would cap residency.
-int choose_groups(const Plan &P, int precision, int tpw, int nsm)
+// Walkers per CTA: 1 for walkers in HBM or groups of more than 256 threads; else the explicit
+// option (refused if G groups do not fit one CTA), then the autotuned choice for this threads
+// per walker, then a heuristic: one, unless the batch has so many small walkers that the
+// 32-CTA-per-SM limit would cap residency.  G x tpw <= 256 and G groups fit one CTA's shared
+// memory (with the drift arrays when a tiled energy pass would keep them there).
+int choose_groups(const Plan &P, const qmc_options *o, int tpw, int dev, int nsm, int &G)
 {
-    if (use_gmem(precision, P.maxpad, tpw)) return 1;
-    int G = 1;
-    if (tpw <= 128 && P.W > 24 * nsm) G = std::min(256 / tpw, (P.W + 24 * nsm - 1) / (24 * nsm));
-    const bool tile = use_tile(precision, P.maxpad, tpw, 1);
-    while (G > 1 && (size_t)G * smem_group(precision, P.maxpad, tpw, tile) > MAX_SMEM) --G;
-    return std::max(1, std::min(G, 8));
+    const int precision = o->precision;
+    G = 1;
+    if (use_gmem(precision, P.maxpad, tpw) || tpw > 256) return QMC_OK;
+    const size_t per = smem_group(precision, P.maxpad, tpw, use_tile(precision, P.maxpad, tpw, 1));
+    const size_t plain = smem_group(precision, P.maxpad, tpw, false);
+    if (o->walkers_per_cta) {
+        G = o->walkers_per_cta;
+        if (G > 1 && ((size_t)G * plain > MAX_SMEM || G * tpw > 256))
+            return fail(QMC_ERR_ARG, "walkers_per_cta = %d groups of %d threads do not fit one CTA", G, tpw);
+        return QMC_OK;
+    }
+    Tuned t;
+    if (tuned_shape(P, o, dev, t) && t.tpw == tpw) {
+        G = t.G;
+    } else if (tpw <= 128 && P.W > 24 * nsm) {
+        G = std::min(256 / tpw, (P.W + 24 * nsm - 1) / (24 * nsm));
+    }
+    while (G > 1 && ((size_t)G * per > MAX_SMEM || G * tpw > 256)) --G;
+    G = std::max(1, std::min(G, 8));
+    return QMC_OK;
 }
 
 // shared memory a launch needs per group and the layout flags that go with it
@@ -580,6 +649,8 @@ int cluster_sweep(const qmc_walker_desc *d, int W, const qmc_options *o, const P
     a.proposal = o->proposal;
     a.sequential = o->sequential;
     a.err = p.ds->err;
+    a.wait_ns = knobs().wait_ns;
+    a.drop_rank = knobs().drop_cluster ? 1 : -1;
     e = launch_sweep_cluster(W * C, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "cluster sweep launch");
     g_launches.fetch_add(1);
@@ -587,7 +658,8 @@ int cluster_sweep(const qmc_walker_desc *d, int W, const qmc_options *o, const P
 }
 
 int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos, double *logpsi, uint64_t *sweep,
-               uint64_t seed, int nsweeps, int energy_every, double *accum, cudaStream_t st, int tpw_force)
+               uint64_t seed, int nsweeps, int energy_every, double *accum, cudaStream_t st, int tpw_force,
+               int g_force = 0)
 {
     int rc;
     if ((rc = check_ptr(pos, "pos", 16)) || (rc = check_ptr(logpsi, "logpsi", 8)) ||
@@ -604,7 +676,12 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
         const int crc = cluster_sweep(d, W, o, P, p, pos, logpsi, sweep, seed, nsweeps, energy_every, accum, st);
         if (crc != -1) return crc;
     }
-    const int G = choose_groups(P, o->precision, tpw, p.ds->nsm);
+    int G = 1;
+    if (g_force) {
+        G = g_force;
+    } else if ((rc = choose_groups(P, o, tpw, p.dev, p.ds->nsm, G))) {
+        return rc;
+    }
     const Shape sh = shape_of(P, o->precision, tpw, G, true, true);
     SweepArgs a;
     a.walkers = P.d_walkers;
@@ -632,6 +709,8 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     a.q_head = a.q_tail = nullptr;
     a.q_slots = nullptr;
     a.q_prog = nullptr;
+    a.wait_ns = knobs().wait_ns;
+    a.drop_push = knobs().drop_queue;
     int grid = (W + G - 1) / G;
     const size_t smem = (size_t)G * sh.smem;
     const Variant v = variant_of(P, o);
@@ -819,7 +898,7 @@ int qmc_pair_hist(const qmc_walker_desc *d, int W, const qmc_options *opt, const
 }
 
 int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const void *pos, void *stream,
-                 int *tpw_out)
+                 int *tpw_out, int *groups_out)
 {
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
@@ -834,36 +913,49 @@ int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const 
     double *lp = nullptr, *acc = nullptr;
     uint64_t *sw = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    int best = 0;
+    Tuned best{0, 0};
     float best_ms = 0;
+    const size_t acc_bytes = sizeof(double) * QMC_ACCUM_FIELDS * (size_t)W;
     cudaError_t e = cudaMalloc(&scratch, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&lp, sizeof(double) * W);
-    if (e == cudaSuccess) e = cudaMalloc(&acc, sizeof(double) * 8 * W);
+    if (e == cudaSuccess) e = cudaMalloc(&acc, acc_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&sw, sizeof(uint64_t) * W);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaMemsetAsync(lp, 0, sizeof(double) * W, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(double) * 8 * W, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, acc_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sw, 0, sizeof(uint64_t) * W, st);
+    // the search space: threads per walker up to one thread per 4-atom partner chunk, walkers per
+    // CTA with at most 256 threads and G groups within one CTA's shared memory (explicit options
+    // narrow it)
     const int chunk_cap = pow2_at_least((P.maxn + 3) / 4);
-    for (int tpw = 32; e == cudaSuccess && tpw <= 1024; tpw <<= 1) {
+    const size_t plain_cap = MAX_SMEM;
+    for (int tpw = 32; e == cudaSuccess && rc == QMC_OK && tpw <= 1024; tpw <<= 1) {
         if (tpw > chunk_cap) break;
-
-        e = cudaMemcpyAsync(scratch, pos, bytes, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) break;
-        rc = sweep_impl(d, W, opt, scratch, lp, sw, 0x7E57ull, 1, 0, acc, st, tpw);  // warm-up
-        if (rc) break;
-        e = cudaEventRecord(e0, st);
-        if (e != cudaSuccess) break;
-        rc = sweep_impl(d, W, opt, scratch, lp, sw, 0x7E57ull, 2, 0, acc, st, tpw);
-        if (rc) break;
-        e = cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
-            best = tpw;
-            best_ms = ms;
+        if (opt->threads_per_walker && tpw != opt->threads_per_walker) continue;
+        const bool gm = use_gmem(opt->precision, P.maxpad, tpw);
+        for (int G = 1; G <= 8; G <<= 1) {
+            if (opt->walkers_per_cta && G != opt->walkers_per_cta) continue;
+            if (G > 1 && (gm || G * tpw > 256 || (size_t)G * smem_group(opt->precision, P.maxpad, tpw, false) > plain_cap))
+                break;
+            if (G > 1 && (W + G - 1) / G < p.ds->nsm / 2) break;  // too few CTAs to fill the GPU
+            e = cudaMemcpyAsync(scratch, pos, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) break;
+            rc = sweep_impl(d, W, opt, scratch, lp, sw, 0x7E57ull, 1, 0, acc, st, tpw, G);  // warm-up
+            if (rc) break;
+            e = cudaEventRecord(e0, st);
+            if (e != cudaSuccess) break;
+            rc = sweep_impl(d, W, opt, scratch, lp, sw, 0x7E57ull, 2, 0, acc, st, tpw, G);
+            if (rc) break;
+            e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (best.tpw == 0 || ms < best_ms)) {
+                best = Tuned{tpw, G};
+                best_ms = ms;
+            }
+            if (e != cudaSuccess) break;
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -875,12 +967,13 @@ int qmc_autotune(const qmc_walker_desc *d, int W, const qmc_options *opt, const 
     cudaFree(sw);
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
-    if (best == 0) return fail(QMC_ERR_CAPACITY, "no admissible threads-per-walker choice");
+    if (best.tpw == 0) return fail(QMC_ERR_CAPACITY, "no admissible launch shape");
     {
         std::lock_guard<std::mutex> lk(g_mu);
         g_tuned[shape_key(p.dev, P, opt)] = best;
     }
-    if (tpw_out) *tpw_out = best;
+    if (tpw_out) *tpw_out = best.tpw;
+    if (groups_out) *groups_out = best.G;
     return QMC_OK;
 }
 
@@ -909,17 +1002,21 @@ int qmc_status(void *stream, int timeout_ms, uint32_t *bits)
             return fail(QMC_ERR_TIMEOUT, "stream not finished after %d ms", timeout_ms);
         std::this_thread::sleep_for(std::chrono::microseconds(100));
     }
-    unsigned h = 0;
+    unsigned h = 0, hs = 0;
+    unsigned *sw = static_error_word(dev);
     cudaError_t e = cudaMemcpyAsync(&h, ds->err, sizeof h, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ds->err, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess && sw) e = cudaMemcpyAsync(&hs, sw, sizeof hs, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && sw) e = cudaMemsetAsync(sw, 0, sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    h |= hs;
     if (bits) *bits = h;
     if (h)
         return fail(QMC_ERR_DEVICE, "kernel flagged %s%s%s%s", (h & QMC_DEVERR_NONFINITE_POS) ? "[bad coordinate]" : "",
                     (h & QMC_DEVERR_NONFINITE_RATIO) ? "[non-finite ratio]" : "",
                     (h & QMC_DEVERR_BAD_INDEX) ? "[atom index out of range]" : "",
-                    (h & QMC_DEVERR_TIMEOUT) ? "[walker queue wait timed out]" : "");
+                    (h & QMC_DEVERR_TIMEOUT) ? "[a bounded device wait timed out]" : "");
     return QMC_OK;
 }
 
@@ -966,6 +1063,14 @@ unsigned char *g_static_dev[MAX_DEVICES];                 // device address of g
 DevWalker g_static_walkers[QMC_STATIC_MAX_WALKERS];       // host staging of the table
 int g_static_order[QMC_STATIC_MAX_WALKERS];               // host staging of the order
 
+unsigned *static_error_word(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_dev[dev]) return nullptr;
+    return reinterpret_cast<unsigned *>(g_static_dev[dev] +
+                                        QMC_STATIC_MAX_WALKERS * (sizeof(DevWalker) + sizeof(int)));
+}
+
 int static_setup(int dev, unsigned char *&base)
 {
     // caller holds g_static_mu; `dev` is the current device
@@ -976,37 +1081,6 @@ int static_setup(int dev, unsigned char *&base)
         g_static_dev[dev] = static_cast<unsigned char *>(p);
     }
     base = g_static_dev[dev];
-    return QMC_OK;
-}
-
-// Validate one descriptor into a table entry (the checks of resolve(), without containers).
-int static_entry(const qmc_walker_desc &x, int w, const qmc_options *o, DevWalker &v)
-{
-    if (x.n < 2) return fail(QMC_ERR_ARG, "walker %d: n = %d < 2", w, x.n);
-    if (x.pad_n < x.n || x.pad_n % 4) return fail(QMC_ERR_ARG, "walker %d: pad_n must be >= n and a multiple of 4", w);
-    if (x.offset < 0 || x.offset % 4) return fail(QMC_ERR_ARG, "walker %d: offset must be >= 0 and a multiple of 4", w);
-    double L = x.L;
-    if (!(L > 0)) {
-        if (!is_fin(x.rho) || x.rho <= 0) return fail(QMC_ERR_ARG, "walker %d: need L > 0 or rho > 0", w);
-        L = std::cbrt((double)x.n / x.rho);
-    }
-    if (!is_fin(L)) return fail(QMC_ERR_ARG, "walker %d: non-finite box side", w);
-    if (!is_fin(x.b) || x.b < 0) return fail(QMC_ERR_ARG, "walker %d: b must be finite and >= 0", w);
-    if (!is_fin(x.m_exp) || x.m_exp <= 0) return fail(QMC_ERR_ARG, "walker %d: m_exp must be finite and > 0", w);
-    if (!is_fin(x.step) || x.step <= 0) return fail(QMC_ERR_ARG, "walker %d: step must be finite and > 0", w);
-    const double reach = o->proposal == QMC_CUBE ? x.step : 6.8 * x.step;
-    if (reach >= L) return fail(QMC_ERR_ARG, "walker %d: step too large for box side %g", w, L);
-    v.n = x.n;
-    v.pad = x.pad_n;
-    v.off = x.offset;
-    v.wid = (uint32_t)x.id;
-    v.slot = w;
-    v.L = L;
-    v.b = x.b;
-    v.m = x.m_exp;
-    v.step = x.step;
-    v.c = -0.5 * std::pow(x.b, x.m_exp);
-    v.K = o->sym ? 2.0 * v.c * std::pow(2.0 / L, x.m_exp) : 0.0;
     return QMC_OK;
 }
 
@@ -1021,6 +1095,12 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     if (rc) return rc;
     if (!d) return fail(QMC_ERR_ARG, "descriptor pointer is NULL");
     if (W <= 0) return fail(QMC_ERR_ARG, "W must be > 0");
+    // the host staging area below is reused by the next call, so a copy recorded into a graph
+    // would read whatever the latest call staged: refuse before anything is enqueued
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(QMC_ERR_ARG, "qmc_sweep_static stages its walker table from host memory reused by the next "
+                                 "call and cannot be recorded during stream capture; call it outside capture");
     if (W > QMC_STATIC_MAX_WALKERS)
         return fail(QMC_ERR_ARG, "qmc_sweep_static takes at most %d walkers (got %d); use qmc_sweep",
                     QMC_STATIC_MAX_WALKERS, W);
@@ -1046,7 +1126,7 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     P.maxn = P.maxpad = 0;
     P.m5 = true;
     for (int w = 0; w < W; ++w) {
-        if ((rc = static_entry(d[w], w, opt, g_static_walkers[w]))) return rc;
+        if ((rc = resolve_one(d[w], w, opt, g_static_walkers[w]))) return rc;
         P.maxn = std::max(P.maxn, d[w].n);
         P.maxpad = std::max(P.maxpad, d[w].pad_n);
         if (d[w].m_exp != 5.0) P.m5 = false;
@@ -1068,7 +1148,8 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     if (e == cudaSuccess && !err) e = cudaMemsetAsync(d_err, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_fail(e, "static walker table upload");
 
-    const int G = choose_groups(P, opt->precision, tpw, nsm);
+    int G = 1;
+    if ((rc = choose_groups(P, opt, tpw, dev, nsm, G))) return rc;
     const Shape sh = shape_of(P, opt->precision, tpw, G, true);
     SweepArgs a;
     a.walkers = d_walkers;
@@ -1097,6 +1178,8 @@ extern "C" int qmc_sweep_static(const qmc_walker_desc *d, int W, const qmc_optio
     a.q_head = a.q_tail = nullptr;
     a.q_slots = nullptr;
     a.q_prog = nullptr;
+    a.wait_ns = knobs().wait_ns;
+    a.drop_push = 0;
     const int grid = (W + G - 1) / G;
     const size_t smem = (size_t)G * sh.smem;
     e = launch_sweep(opt->precision, tpw, variant_of(P, opt), grid, G * tpw, smem, st, a);

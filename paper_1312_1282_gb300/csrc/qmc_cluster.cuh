@@ -33,6 +33,9 @@ struct ClusterArgs {
     int nsweeps;
     int proposal, sequential;
     unsigned *err;
+    unsigned long long wait_ns;  // limit of every exchange wait (global-timer nanoseconds)
+    int drop_rank;               // failure test only: this CTA rank of the first walker's cluster
+                                 // never stores or arrives, so its peers' waits run out (-1 normally)
 };
 
 constexpr int CLUSTER_TPW = 512;  // threads per CTA (one CTA per SM: 512 x 128 registers)
@@ -81,9 +84,10 @@ __device__ __forceinline__ bool mb_test_cluster(unsigned addr, unsigned parity)
     return done != 0;
 }
 
-// bounded like every other wait: 10 s of global time, then QMC_DEVERR_TIMEOUT; once that bit is
-// set, later waits fail at once
-__device__ __forceinline__ bool mb_wait_cluster(unsigned long long *mb, unsigned parity, unsigned *err)
+// bounded like every other wait: the call's limit of global time (10 s unless a failure test
+// shortens it), then QMC_DEVERR_TIMEOUT; once that bit is set, later waits fail at once
+__device__ __forceinline__ bool mb_wait_cluster(unsigned long long *mb, unsigned parity, unsigned long long limit_ns,
+                                                unsigned *err)
 {
     const unsigned addr = smem_u32(mb);
     unsigned long long t0 = 0;
@@ -94,7 +98,7 @@ __device__ __forceinline__ bool mb_wait_cluster(unsigned long long *mb, unsigned
             const unsigned long long now = global_ns();
             if (t0 == 0)
                 t0 = now;
-            else if (now - t0 > 10000000000ull)
+            else if (now - t0 > limit_ns)
                 break;
         }
     }
@@ -149,6 +153,7 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
     cluster_sync_all();  // every CTA's mbarriers exist before the first remote arrive
 
     const DevWalker d = a.walkers[blockIdx.x / C];
+    const bool mute = blockIdx.x / C == 0 && (int)rank == a.drop_rank;  // failure test only
     const int n = d.n;
     const int S = ((n + C - 1) / C + 3) & ~3;  // this walker's slice (multiple of 4, <= a.slice)
     const int j0 = (int)rank * S;
@@ -176,7 +181,7 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
         __syncthreads();
         const unsigned ph = jx & 1u, par = (jx >> 1) & 1u;
         ++jx;
-        if (gtid < K) {
+        if (gtid < K && !mute) {
             float s = red[gtid * NW];
 #pragma unroll
             for (int w = 1; w < NW; ++w) s += red[gtid * NW + w];
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
                 mb_arrive_remote(map_rank(&mb[ph], (unsigned)r));
             }
         }
-        if (!tmo && !mb_wait_cluster(&mb[ph], par, a.err)) tmo = true;
+        if (!tmo && !mb_wait_cluster(&mb[ph], par, a.wait_ns, a.err)) tmo = true;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             const float *p = &part[(ph * K + i) * 8];
@@ -447,7 +452,7 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
             gx[2 * (size_t)d.pad + j0 + i] = sz[i];
         }
         if (gtid == 0 && rank == 0) {
-            a.accum[8 * (size_t)d.slot + 7] += (double)nacc;
+            a.accum[QMC_ACCUM_FIELDS * (size_t)d.slot + 7] += (double)nacc;
             a.logpsi[d.slot] = lp.value();
             a.sweep[d.slot] = k0 + (unsigned long long)a.nsweeps;
         }

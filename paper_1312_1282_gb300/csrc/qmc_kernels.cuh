@@ -118,6 +118,9 @@ struct SweepArgs {
     unsigned *q_head, *q_tail;
     uint2 *q_slots;          // [W] {sequence, walker table index}
     int *q_prog;             // [W] chunks done (bit 30: walker faulted, its chunks are skipped)
+    unsigned long long wait_ns;  // limit of every wait on the queue (global-timer nanoseconds)
+    int drop_push;           // failure test only: the first walker of the order is never pushed back
+                             // after its first chunk, so pops that wait for it run out (0 normally)
 };
 
 // Moves per batch of the FP32 sweep: the partner loop serves KB trial moves at once and the
@@ -135,10 +138,10 @@ template <typename T, int TPW> constexpr int kb_of() { return std::is_same<T, fl
 
 // Shared memory of one group, in this order: positions x | y | z (stride elements of T each),
 // reduction slots (2 phases of TPW/32 doubles, 2 phases of KB x TPW/32 T's), the cross terms of
-// a batch (2 phases of KB x KB T's), a broadcast word, two mbarriers, and with the tiled energy
-// pass the drift components Fx | Fy | Fz (stride floats each).
+// a batch (2 phases of KB x KB T's), a broadcast word, and with the tiled energy pass the drift
+// components Fx | Fy | Fz (stride floats each).
 struct GroupLayout {
-    size_t red, redT, dsm, bc, mb, F, bytes;
+    size_t red, redT, dsm, bc, F, bytes;
 };
 template <typename T> __host__ __device__ constexpr GroupLayout group_layout(int stride, int tpw, bool tile)
 {
@@ -147,8 +150,7 @@ template <typename T> __host__ __device__ constexpr GroupLayout group_layout(int
     g.redT = g.red + (size_t)2 * (tpw / 32) * sizeof(double);
     g.dsm = g.redT + (size_t)2 * KB * (tpw / 32) * sizeof(T);
     g.bc = (g.dsm + (size_t)2 * KB * KB * sizeof(T) + 15) / 16 * 16;
-    g.mb = g.bc + 16;  // two mbarriers (8 bytes each) of the pipelined moves
-    g.F = g.mb + 16;
+    g.F = g.bc + 16;
     g.bytes = g.F + (tile ? (size_t)3 * stride * sizeof(float) : 0);
     return g;
 }
@@ -163,12 +165,10 @@ template <typename T> struct GroupMem {
     double *redD;
     float *fx, *fy, *fz;
     int *bc;  // one int broadcast from the group's thread 0
-    unsigned long long *mb;  // two mbarriers (pipelined moves)
     __device__ __forceinline__ void bind(unsigned char *base, int stride, int tpw, bool tile)
     {
         const GroupLayout g = group_layout<T>(stride, tpw, tile);
         bc = reinterpret_cast<int *>(base + g.bc);
-        mb = reinterpret_cast<unsigned long long *>(base + g.mb);
         sx = reinterpret_cast<T *>(base);
         sy = sx + stride;
         sz = sy + stride;
@@ -915,31 +915,8 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
 }
 
 // ----------------------------------------------------------------------------------------------
-// Pipelined moves (FP32, exponent 5, symmetrised u, groups of 64 threads or more; off by default,
-// build with -DQMC_PIPE=1).  The group sum of move i goes through an mbarrier instead of a full
-// barrier: every warp stores its partial sum and arrives, the threads go on with the partner
-// loop of move i+1 -- in which the atom of move i is masked like the moved atom -- and only then
-// wait for the partials of move i and take its decision.  The owner of move i's atom then adds
-// the pair term of that atom, at its decided position, to its partial sum of move i+1, so the
-// partner sum of Eq. (JastrowUpdate) is the masked loop plus that one term.  Two mbarriers
-// alternate: move j (a counter kept per group for the whole launch) uses barrier j & 1, phase
-// parity (j >> 1) & 1.  A move of the pending move's atom decides the pending move first.
-// Measured at N = 1952, 528 walkers, 128 threads per walker: 20.1 ms per 5 sweeps against 18.7
-// for one barrier per move (the other walkers on the SM already fill the barrier's bubbles, and
-// the pending atom's term lies on the critical path), so the single-barrier path is the default.
+// Helpers of the bounded waits and of the cluster sweep
 // ----------------------------------------------------------------------------------------------
-#ifndef QMC_PIPE
-#define QMC_PIPE 0
-#endif
-#ifndef QMC_PIPE_UNROLL
-#define QMC_PIPE_UNROLL 1
-#endif
-constexpr int PIPE_UNROLL = QMC_PIPE_UNROLL;
-template <typename T, int MEXP, bool SYM, int TPW> constexpr bool pipe_moves()
-{
-    return QMC_PIPE && std::is_same<T, float>::value && MEXP == 5 && SYM && kb_of<T, TPW>() == 1 && TPW >= 64;
-}
-
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -952,91 +929,6 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)_
 __device__ __forceinline__ void mb_init(unsigned long long *mb, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mb_arrive(unsigned long long *mb)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(mb))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mb_test(unsigned addr, unsigned parity)
-{
-    unsigned done;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(done)
-                 : "r"(addr), "r"(parity)
-                 : "memory");
-    return done != 0;
-}
-
-// Wait for the phase of the given parity to complete.  Bounded: 10 s of global time, after
-// which QMC_DEVERR_TIMEOUT is set; once that bit is set every later wait fails at once.
-__device__ __forceinline__ bool mb_wait(unsigned long long *mb, unsigned parity, unsigned *err)
-{
-    const unsigned addr = smem_u32(mb);
-    unsigned long long t0 = 0;
-    for (unsigned it = 0; it < (1u << 30); ++it) {
-        if (mb_test(addr, parity)) return true;
-        if ((it & 255) == 255) {  // the clock and the error word only now and then
-            if (*reinterpret_cast<volatile unsigned *>(err) & QMC_DEVERR_TIMEOUT) return false;
-            const unsigned long long now = global_ns();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > 10000000000ull) break;
-        }
-    }
-    atomicOr(err, QMC_DEVERR_TIMEOUT);
-    return false;
-}
-
-// This thread's partner sum of one move, c (sum_new - sum_old) over its chunks, with the moved
-// atom s and the pending atom s2 (or -1) masked by NaN.
-template <int TPW, bool GM>
-__device__ __forceinline__ float partners_pipe(const Jas<float, 5, true> &J, const float *sx, const float *sy,
-                                               const float *sz, int n, int nv, int s, int s2, float ax, float ay,
-                                               float az, float bx, float by, float bz, int gtid)
-{
-    Packed5 P;
-    P.init(J);
-    const int cs = s >> 2, cs2 = s2 >= 0 ? s2 >> 2 : -1;
-    const float2 nax = make_float2(-ax, -ax), nay = make_float2(-ay, -ay), naz = make_float2(-az, -az);
-    const float2 nbx = make_float2(-bx, -bx), nby = make_float2(-by, -by), nbz = make_float2(-bz, -bz);
-    float2 acco = make_float2(0.f, 0.f), accn = make_float2(0.f, 0.f);
-#pragma unroll PIPE_UNROLL
-    for (int c = gtid; c < nv; c += TPW) {
-        float4 X = reinterpret_cast<const float4 *>(sx)[c];
-        float4 Y = reinterpret_cast<const float4 *>(sy)[c];
-        float4 Z = reinterpret_cast<const float4 *>(sz)[c];
-        if (c == cs) {
-            const int e = s - 4 * c;
-            Vec<float>::set(X, e, qnan<float>());
-            Vec<float>::set(Y, e, qnan<float>());
-            Vec<float>::set(Z, e, qnan<float>());
-        }
-        if (c == cs2) {
-            const int e = s2 - 4 * c;
-            Vec<float>::set(X, e, qnan<float>());
-            Vec<float>::set(Y, e, qnan<float>());
-            Vec<float>::set(Z, e, qnan<float>());
-        }
-        if (GM && c == nv - 1)  // entries past n (HBM padding of a walker used in place)
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (4 * c + e >= n) {
-                    Vec<float>::set(X, e, qnan<float>());
-                    Vec<float>::set(Y, e, qnan<float>());
-                    Vec<float>::set(Z, e, qnan<float>());
-                }
-        const float2 xa = make_float2(X.x, X.y), xb = make_float2(X.z, X.w);
-        const float2 ya = make_float2(Y.x, Y.y), yb = make_float2(Y.z, Y.w);
-        const float2 za = make_float2(Z.x, Z.y), zb = make_float2(Z.z, Z.w);
-        P.acc5(__fadd2_rn(xa, nax), __fadd2_rn(ya, nay), __fadd2_rn(za, naz), acco);
-        P.acc5(__fadd2_rn(xa, nbx), __fadd2_rn(ya, nby), __fadd2_rn(za, nbz), accn);
-        P.acc5(__fadd2_rn(xb, nax), __fadd2_rn(yb, nay), __fadd2_rn(zb, naz), acco);
-        P.acc5(__fadd2_rn(xb, nbx), __fadd2_rn(yb, nby), __fadd2_rn(zb, nbz), accn);
-    }
-    return J.c * ((accn.x + accn.y) - (acco.x + acco.y));
 }
 
 // u(|b - r|) - u(|a - r|) of one partner at r, in the same arithmetic as the partner loop
@@ -1059,7 +951,7 @@ __device__ __forceinline__ float cross5(const Jas<float, 5, true> &J, float ax, 
 // ----------------------------------------------------------------------------------------------
 template <typename T, int MEXP, bool SYM, int TPW, bool GM>
 __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> mem, int gtid, int bar_id,
-                          long long m_begin, long long m_end, bool last, unsigned &jm)
+                          long long m_begin, long long m_end, bool last)
 {
     // GM: the walker is used in place in HBM; otherwise it is copied to shared memory (the
     // address space is a compile-time property so that shared loads stay shared loads)
@@ -1087,7 +979,7 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
     LogPsiAcc<T> lp;
     lp.set(a.logpsi[slot]);
     const unsigned long long k0 = a.sweep[slot];
-    double *A = a.accum + 8 * (size_t)slot;
+    double *A = a.accum + QMC_ACCUM_FIELDS * (size_t)slot;
     int nacc = 0;
     constexpr int K = kb_of<T, TPW>();  // moves per batch
     Recent<T, K> rec;
@@ -1095,84 +987,6 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
     const int lane = gtid & 31;
     const uint32_t wid = d.wid;
     T *dsm = mem.dsm;  // cross terms of a batch
-
-    // pipelined moves: the move whose decision is pending
-    constexpr bool PIPE = pipe_moves<T, MEXP, SYM, TPW>();
-    bool pend = false;
-    int ps = 0;
-    unsigned pj = 0;
-    T pax = 0, pay = 0, paz = 0, pbx = 0, pby = 0, pbz = 0, pxi = 0;
-    // wait for the partial sums of the pending move and decide it (Eq. Decision: 2 Delta > ln xi)
-    auto pipe_resolve = [&](bool &accepted) -> bool {
-        constexpr int NW = TPW / 32;
-        pend = false;
-        if (!mb_wait(mem.mb + (pj & 1u), (pj >> 1) & 1u, a.err)) return false;
-        const T *r = redT + (pj & 1u) * NW;
-        T S = r[0];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) S += r[w];
-        if (S != S) {
-            if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
-            return false;
-        }
-        accepted = (T)2 * S > pxi;
-        rec.clear();  // the writes of the move before the pending one are visible after the wait
-        if (accepted) {
-            if (gtid == 0) lp.add(S);
-            ++nacc;
-            if (gtid == (ps / VN) % TPW) {
-                sx[ps] = pbx;
-                sy[ps] = pby;
-                sz[ps] = pbz;
-            }
-            rec.add(ps, pbx, pby, pbz);
-        }
-        return true;
-    };
-    // One move.  prev is the atom of the previous move of the same 32-move block (-1 for the first
-    // move of a block).  Unless it is this move's atom, it is masked in the loop and its owner adds
-    // its pair term at its decided position: the arithmetic of a move depends only on its place in
-    // its block, not on where a call or a chunk of the persistent queue began or ended.
-    auto pipe_move = [&](int s, T dx, T dy, T dz, T lxi, int prev) -> bool {
-        if constexpr (PIPE) {
-            bool acc_p = false;
-            if (pend && s == ps) {  // the pending move's atom moves again: decide that move first
-                if (!pipe_resolve(acc_p)) return false;
-                group_sync<TPW>(bar_id);
-                rec.clear();
-            }
-            const int m2 = (prev >= 0 && prev != s) ? prev : -1;
-            T ax = sx[s], ay = sy[s], az = sz[s];
-            rec.lookup(s, ax, ay, az);
-            const T bx = wrap(ax + dx, L), by = wrap(ay + dy, L), bz = wrap(az + dz, L);
-            T part = partners_pipe<TPW, GM>(J, sx, sy, sz, n, nv, s, m2, ax, ay, az, bx, by, bz, gtid);
-            if (pend) {  // m2 == ps: decide it, then its owner adds its term
-                if (!pipe_resolve(acc_p)) return false;
-                if (gtid == (ps / VN) % TPW)
-                    part += cross5(J, ax, ay, az, bx, by, bz, acc_p ? pbx : pax, acc_p ? pby : pay,
-                                   acc_p ? pbz : paz);
-            } else if (m2 >= 0 && gtid == (m2 / VN) % TPW) {  // decided in an earlier call or chunk
-                part += cross5(J, ax, ay, az, bx, by, bz, sx[m2], sy[m2], sz[m2]);
-            }
-            part = warp_sum(part);
-            const unsigned j = jm++;
-            if ((gtid & 31) == 0) {
-                redT[(j & 1u) * (TPW / 32) + (gtid >> 5)] = part;
-                mb_arrive(mem.mb + (j & 1u));
-            }
-            pend = true;
-            pj = j;
-            ps = s;
-            pax = ax;
-            pay = ay;
-            paz = az;
-            pbx = bx;
-            pby = by;
-            pbz = bz;
-            pxi = lxi;
-        }
-        return true;
-    };
 
     for (long long m = m_begin; m < m_end;) {
         const long long it = m / n;
@@ -1212,66 +1026,64 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
             if constexpr (std::is_same<T, float>::value) mxi = logf(mxi);
             const int cnt = min(32, t_stop - t0);
             int tt = max(0, t_start - t0);
-            if constexpr (PIPE) {
-                for (; tt < cnt; ++tt) {
-                    const int prev = __shfl_sync(FULL, my_s, (tt + 31) & 31);
-                    if (!pipe_move(__shfl_sync(FULL, my_s, tt), __shfl_sync(FULL, mdx, tt), __shfl_sync(FULL, mdy, tt),
-                                   __shfl_sync(FULL, mdz, tt), __shfl_sync(FULL, mxi, tt), tt > 0 ? prev : -1))
-                        return false;
+            for (; tt + K <= cnt; tt += K) {
+                int bs[K];
+                T bdx[K], bdy[K], bdz[K], bxi[K];
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    bs[i] = __shfl_sync(FULL, my_s, tt + i);
+                    bdx[i] = __shfl_sync(FULL, mdx, tt + i);
+                    bdy[i] = __shfl_sync(FULL, mdy, tt + i);
+                    bdz[i] = __shfl_sync(FULL, mdz, tt + i);
+                    bxi[i] = __shfl_sync(FULL, mxi, tt + i);
                 }
-                bool acc_p;  // the block's last move is decided before the next block
-                if (pend && !pipe_resolve(acc_p)) return false;
-            } else {
-                for (; tt + K <= cnt; tt += K) {
-                    int bs[K];
-                    T bdx[K], bdy[K], bdz[K], bxi[K];
+                bool distinct = true;
 #pragma unroll
-                    for (int i = 0; i < K; ++i) {
-                        bs[i] = __shfl_sync(FULL, my_s, tt + i);
-                        bdx[i] = __shfl_sync(FULL, mdx, tt + i);
-                        bdy[i] = __shfl_sync(FULL, mdy, tt + i);
-                        bdz[i] = __shfl_sync(FULL, mdz, tt + i);
-                        bxi[i] = __shfl_sync(FULL, mxi, tt + i);
-                    }
-                    bool distinct = true;
+                for (int i = 0; i < K; ++i)
 #pragma unroll
-                    for (int i = 0; i < K; ++i)
-#pragma unroll
-                        for (int q = i + 1; q < K; ++q) distinct &= bs[i] != bs[q];
-                    bool ok = true;
-                    if (distinct) {
-                        ok = move_batch<T, MEXP, SYM, TPW, K, K, GM>(J, sx, sy, sz, n, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
-                                                                   nacc, redT, dsm, phT, bar_id, gtid);
-                    } else {
-                        for (int i = 0; i < K && ok; ++i) {
-                            const int s1[1] = {bs[i]};
-                            const T x1[1] = {bdx[i]}, y1[1] = {bdy[i]}, z1[1] = {bdz[i]}, c1[1] = {bxi[i]};
-                            ok = move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp,
-                                                                      nacc, redT, dsm, phT, bar_id, gtid);
-                        }
-                    }
-                    if (!ok) {
-                        if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
-                        return false;
+                    for (int q = i + 1; q < K; ++q) distinct &= bs[i] != bs[q];
+                bool ok = true;
+                if (distinct) {
+                    ok = move_batch<T, MEXP, SYM, TPW, K, K, GM>(J, sx, sy, sz, n, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
+                                                               nacc, redT, dsm, phT, bar_id, gtid);
+                } else {
+                    for (int i = 0; i < K && ok; ++i) {
+                        const int s1[1] = {bs[i]};
+                        const T x1[1] = {bdx[i]}, y1[1] = {bdy[i]}, z1[1] = {bdz[i]}, c1[1] = {bxi[i]};
+                        ok = move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp,
+                                                                  nacc, redT, dsm, phT, bar_id, gtid);
                     }
                 }
-                for (; tt < cnt; ++tt) {
-                    const int s1[1] = {__shfl_sync(FULL, my_s, tt)};
-                    const T x1[1] = {__shfl_sync(FULL, mdx, tt)}, y1[1] = {__shfl_sync(FULL, mdy, tt)},
-                            z1[1] = {__shfl_sync(FULL, mdz, tt)}, c1[1] = {__shfl_sync(FULL, mxi, tt)};
-                    if (!move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
-                                                              dsm, phT, bar_id, gtid)) {
-                        if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
-                        return false;
-                    }
+                if (!ok) {
+                    if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
+                    return false;
+                }
+            }
+            for (; tt < cnt; ++tt) {
+                const int s1[1] = {__shfl_sync(FULL, my_s, tt)};
+                const T x1[1] = {__shfl_sync(FULL, mdx, tt)}, y1[1] = {__shfl_sync(FULL, mdy, tt)},
+                        z1[1] = {__shfl_sync(FULL, mdz, tt)}, c1[1] = {__shfl_sync(FULL, mxi, tt)};
+                if (!move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
+                                                          dsm, phT, bar_id, gtid)) {
+                    if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
+                    return false;
                 }
             }
         }
         if (t_stop < n) break;  // the range ends inside this sweep
         group_sync<TPW>(bar_id);
         rec.clear();
-        if (a.recompute_every > 0 && (kk + 1) % (unsigned long long)a.recompute_every == 0)
-            lp.set(group_log_psi<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, redD, phD, bar_id, gtid));
+        if (a.recompute_every > 0 && (kk + 1) % (unsigned long long)a.recompute_every == 0) {
+            // Eq. (Jastrow) from scratch; the drift of the carried sum (thread 0 carries it) is
+            // recorded before it is replaced
+            const double fresh = group_log_psi<T, MEXP, SYM, TPW>(J, sx, sy, sz, n, nv, redD, phD, bar_id, gtid);
+            if (gtid == 0) {
+                const double drift = fabs(lp.value() - fresh);
+                A[8] += drift;
+                A[9] = fmax(A[9], drift);
+            }
+            lp.set(fresh);
+        }
         if (a.energy_every > 0 && (kk + 1) % (unsigned long long)a.energy_every == 0) {
             double e[5];
             if constexpr (std::is_same<T, float>::value && !GM) {
@@ -1311,15 +1123,17 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
 // frees the slot (sequence p + W); the push of ticket p waits for sequence p, stores the walker
 // and publishes it (sequence p + 1).  It starts full (all W walkers) and exactly W walkers
 // circulate, so a push finds its slot free as soon as the matching pop has left it.  Every wait
-// is bounded (10 s of global time); on expiry the error word gets QMC_DEVERR_TIMEOUT.
+// is bounded (the call's limit, 10 s of global time unless a failure test shortens it); on expiry
+// the error word gets QMC_DEVERR_TIMEOUT.
 // ----------------------------------------------------------------------------------------------
-__device__ __forceinline__ bool wait_seq(unsigned *seq_word, unsigned want, unsigned *err)
+__device__ __forceinline__ bool wait_seq(unsigned *seq_word, unsigned want, unsigned long long limit_ns,
+                                         unsigned *err)
 {
     cuda::atomic_ref<unsigned, cuda::thread_scope_device> seq(*seq_word);
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0; it < (1u << 30); ++it) {
         if (seq.load(cuda::memory_order_acquire) == want) return true;
-        if ((it & 63) == 63 && global_ns() - t0 > 10000000000ull) break;
+        if ((it & 63) == 63 && global_ns() - t0 > limit_ns) break;
         __nanosleep(128);
     }
     atomicOr(err, QMC_DEVERR_TIMEOUT);
@@ -1332,7 +1146,7 @@ __device__ __forceinline__ int queue_pop(const SweepArgs &a, unsigned total)
     const unsigned pos = atomicAdd(a.q_head, 1u);
     if (pos >= total) return -1;
     uint2 *sl = a.q_slots + pos % (unsigned)a.W;
-    if (!wait_seq(&sl->x, pos + 1, a.err)) return -1;
+    if (!wait_seq(&sl->x, pos + 1, a.wait_ns, a.err)) return -1;
     const int w = (int)*reinterpret_cast<volatile unsigned *>(&sl->y);
     cuda::atomic_ref<unsigned, cuda::thread_scope_device>(sl->x).store(pos + (unsigned)a.W,
                                                                        cuda::memory_order_release);
@@ -1343,7 +1157,7 @@ __device__ __forceinline__ void queue_push(const SweepArgs &a, int w)
 {
     const unsigned pos = atomicAdd(a.q_tail, 1u);
     uint2 *sl = a.q_slots + pos % (unsigned)a.W;
-    if (!wait_seq(&sl->x, pos, a.err)) return;
+    if (!wait_seq(&sl->x, pos, a.wait_ns, a.err)) return;
     *reinterpret_cast<volatile unsigned *>(&sl->y) = (unsigned)w;
     cuda::atomic_ref<unsigned, cuda::thread_scope_device>(sl->x).store(pos + 1, cuda::memory_order_release);
 }
@@ -1352,7 +1166,7 @@ __device__ __forceinline__ void queue_push(const SweepArgs &a, int w)
 
 // Persistent mode: take ready walkers from the FIFO, advance each by one chunk, put it back.
 template <typename T, int MEXP, bool SYM, int TPW>
-__device__ __forceinline__ void persistent_loop(const SweepArgs &a, GroupMem<T> mem, int g, int gtid, unsigned &jm)
+__device__ __forceinline__ void persistent_loop(const SweepArgs &a, GroupMem<T> mem, int g, int gtid)
 {
     constexpr int DEAD = 1 << 30;
     for (;;) {
@@ -1370,14 +1184,16 @@ __device__ __forceinline__ void persistent_loop(const SweepArgs &a, GroupMem<T> 
         const long long m1 = min(total, m0 + a.chunk_moves);
         bool ok = true;
         if (!(c & DEAD))
-            ok = a.gmem ? run_range<T, MEXP, SYM, TPW, true>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total, jm)
-                        : run_range<T, MEXP, SYM, TPW, false>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total, jm);
+            ok = a.gmem ? run_range<T, MEXP, SYM, TPW, true>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total)
+                        : run_range<T, MEXP, SYM, TPW, false>(a, d, mem, gtid, 1 + g, m0, m1, m1 == total);
         __threadfence();  // this thread's stores of the walker state, before it is handed on
         group_sync<TPW>(1 + g);
         if (gtid == 0) {
             a.q_prog[w] = (c + 1) | (ok ? 0 : DEAD);
             __threadfence();
-            if (m1 < total) queue_push(a, w);
+            // (a failure test drops one push: the pops that wait for it run out, bounded)
+            const bool dropped = a.drop_push && c == 0 && w == a.order[0];
+            if (m1 < total && !dropped) queue_push(a, w);
         }
     }
 }
@@ -1398,24 +1214,16 @@ __global__ void __launch_bounds__(cta_bound<TPW>(), min_blocks<TPW>()) sweep_ker
     GroupMem<T> mem;
     mem.bind(smem + (size_t)g * group_smem<T>(a.stride, TPW, a.tile == 1), a.stride, TPW, a.tile == 1);
     if (a.tile == 2) mem.use_global_drift(a.fscr + (size_t)3 * a.stride * (blockIdx.x * a.G + g), a.stride);
-    unsigned jm = 0;  // pipelined moves arrived on the group's mbarriers
-    if constexpr (pipe_moves<T, MEXP, SYM, TPW>()) {
-        if (gtid == 0) {
-            mb_init(mem.mb, TPW / 32);
-            mb_init(mem.mb + 1, TPW / 32);
-        }
-        group_sync<TPW>(1 + g);
-    }
     if (!a.dynamic) {
         const DevWalker d = a.walkers[a.order[item]];
         const long long total = (long long)a.nsweeps * d.n;
         if (a.gmem)
-            run_range<T, MEXP, SYM, TPW, true>(a, d, mem, gtid, 1 + g, 0, total, true, jm);
+            run_range<T, MEXP, SYM, TPW, true>(a, d, mem, gtid, 1 + g, 0, total, true);
         else
-            run_range<T, MEXP, SYM, TPW, false>(a, d, mem, gtid, 1 + g, 0, total, true, jm);
+            run_range<T, MEXP, SYM, TPW, false>(a, d, mem, gtid, 1 + g, 0, total, true);
         return;
     }
-    persistent_loop<T, MEXP, SYM, TPW>(a, mem, g, gtid, jm);
+    persistent_loop<T, MEXP, SYM, TPW>(a, mem, g, gtid);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -1432,7 +1240,6 @@ __global__ void __launch_bounds__(TPWB, TPWB <= 256 ? 2 : 1) sweep_mixed_kernel(
 {
     static_assert(TPWB % TPWS == 0 && TPWB / TPWS <= 15, "groups of the second phase");
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned jm = 0;
     {
         GroupMem<T> mem;
         mem.bind(smem, big.stride, TPWB, big.tile == 1);
@@ -1445,7 +1252,7 @@ __global__ void __launch_bounds__(TPWB, TPWB <= 256 ? 2 : 1) sweep_mixed_kernel(
             group_sync<TPWB>(1);
             if (i >= big.W) break;
             const DevWalker d = big.walkers[big.order[i]];
-            run_range<T, MEXP, SYM, TPWB, false>(big, d, mem, gtid, 1, 0, (long long)big.nsweeps * d.n, true, jm);
+            run_range<T, MEXP, SYM, TPWB, false>(big, d, mem, gtid, 1, 0, (long long)big.nsweeps * d.n, true);
             group_sync<TPWB>(1);
         }
     }
@@ -1454,7 +1261,7 @@ __global__ void __launch_bounds__(TPWB, TPWB <= 256 ? 2 : 1) sweep_mixed_kernel(
     GroupMem<T> mem;
     mem.bind(smem + (size_t)g * group_smem<T>(a.stride, TPWS, a.tile == 1), a.stride, TPWS, a.tile == 1);
     if (a.tile == 2) mem.use_global_drift(a.fscr + (size_t)3 * a.stride * (blockIdx.x * a.G + g), a.stride);
-    persistent_loop<T, MEXP, SYM, TPWS>(a, mem, g, gtid, jm);
+    persistent_loop<T, MEXP, SYM, TPWS>(a, mem, g, gtid);
 }
 
 // ----------------------------------------------------------------------------------------------

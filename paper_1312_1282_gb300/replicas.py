@@ -25,7 +25,8 @@ def walker_ids(rank: int, world: int, per_rank: int) -> list[int]:
 def block_stats(accum: torch.Tensor, n_atoms: torch.Tensor | float, group=None) -> dict:
     """Energy per atom over all walkers of all ranks, with the standard error across walkers.
 
-    accum: [W, 8] per-walker sums {E_L, E_L^2, V, T_L, T_PB, T_F, samples, accepted} (this rank).
+    accum: [W, >= 8] per-walker sums {E_L, E_L^2, V, T_L, T_PB, T_F, samples, accepted, ...} (this
+    rank; the ln psi drift fields that follow are not used here).
     Each walker's time average is one independent estimate (Eq. CorrelatedError with independent
     chains); their spread gives the error bar.  With torch.distributed initialised, the sums
     over walkers are all-reduced (float64, on the host)."""

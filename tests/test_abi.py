@@ -22,7 +22,7 @@ def _declared():
 def test_library_builds_and_loads():
     q._build.build()
     assert os.path.exists(q._build.LIB)
-    assert q.qmc_version() == 100
+    assert q.qmc_version() == 110
 
 
 def test_every_declared_symbol_is_exported():
@@ -38,9 +38,13 @@ def test_every_declared_symbol_is_exported():
 
 def test_struct_layouts_match_header():
     assert C.sizeof(q.WalkerDesc) == 64
-    assert C.sizeof(q.Options) == 32
+    assert C.sizeof(q.Options) == 40
     assert q.WalkerDesc.offset.offset == 8 and q.WalkerDesc.L.offset == 24 and q.WalkerDesc.step.offset == 56
     assert q.Options.hbar2_over_m.offset == 16 and q.Options.threads_per_walker.offset == 28
+    assert q.Options.walkers_per_cta.offset == 32 and q.Options.reserved.offset == 36
+    src = open(HEADER).read()
+    assert int(re.search(r"#define QMC_ACCUM_FIELDS (\d+)", src).group(1)) == q.NACC == 10
+    assert int(re.search(r"#define QMC_VERSION (\d+)", src).group(1)) == 110
 
 
 def test_capacity_matches_shared_memory():
@@ -57,6 +61,13 @@ def test_host_side_argument_errors_need_no_device():
         q.qmc_local_energy(d, bad, 16, 16, stream=0)
     with pytest.raises(q.QmcError, match="ARG"):
         q.qmc_local_energy(d, q.options(threads_per_walker=48), 16, 16, stream=0)
+    for kw in (dict(walkers_per_cta=9), dict(walkers_per_cta=-1), dict(walkers_per_cta=4, threads_per_walker=128)):
+        with pytest.raises(q.QmcError, match="ARG"):
+            q.qmc_local_energy(d, q.options(**kw), 16, 16, stream=0)
+    o = q.options()
+    o.reserved = 1
+    with pytest.raises(q.QmcError, match="reserved"):
+        q.qmc_local_energy(d, o, 16, 16, stream=0)
     with pytest.raises(q.QmcError, match="ARG"):
         q.qmc_sweep(d, q.options(), 16, 16, 16, 0, -1, 0, 16, stream=0)
     with pytest.raises(q.QmcError, match="ARG"):   # misaligned position pointer

@@ -31,7 +31,7 @@ def _oracle_chain(P, w, seed, nsw, every, opt, k0=0, lp0=None, margins=False):
 def _gpu_chain(P, seed, nsw, every, opt):
     lp = zeros(P.W)
     q.qmc_log_psi(P.d, opt, P.pos, lp)
-    sw, acc = zeros(P.W, torch.int64), zeros((P.W, 8))
+    sw, acc = zeros(P.W, torch.int64), zeros((P.W, q.NACC))
     q.qmc_sweep(P.d, opt, P.pos, lp, sw, seed, nsw, every, acc)
     assert q.qmc_status(timeout_ms=120000) == 0
     return lp.cpu().numpy(), sw.cpu().numpy(), acc.cpu().numpy()
@@ -113,8 +113,8 @@ def test_resume_is_bitwise_identical():
         A = lattice_batch([64, 130, 512], prec, seed=5)
         B = lattice_batch([64, 130, 512], prec, seed=5)
         opt = q.options(precision=prec, recompute_every=3)
-        la, sa, aa = zeros(3), zeros(3, torch.int64), zeros((3, 8))
-        lb, sb, ab = zeros(3), zeros(3, torch.int64), zeros((3, 8))
+        la, sa, aa = zeros(3), zeros(3, torch.int64), zeros((3, q.NACC))
+        lb, sb, ab = zeros(3), zeros(3, torch.int64), zeros((3, q.NACC))
         q.qmc_sweep(A.d, opt, A.pos, la, sa, 11, 10, 2, aa)
         q.qmc_sweep(B.d, opt, B.pos, lb, sb, 11, 4, 2, ab)
         q.qmc_sweep(B.d, opt, B.pos, lb, sb, 11, 6, 2, ab)
@@ -127,14 +127,14 @@ def test_autotune_keeps_the_chain():
     P = lattice_batch([512] * 8, q.QMC_FP32, seed=6)
     Q = lattice_batch([512] * 8, q.QMC_FP32, seed=6)
     opt = q.options(precision=q.QMC_FP32)
-    t = q.qmc_autotune(P.d, opt, P.pos)
-    assert t in (32, 64, 128, 256, 512, 1024)
+    t, g = q.qmc_autotune(P.d, opt, P.pos)
+    assert t in (32, 64, 128, 256, 512, 1024) and g in (1, 2, 4, 8) and g * t <= max(256, t)
     torch.cuda.synchronize()
     assert torch.equal(P.pos, Q.pos)  # tuning runs on a scratch copy
     for shape in (t, 32):
         o = q.options(precision=q.QMC_FP32, threads_per_walker=shape)
         R = lattice_batch([512] * 8, q.QMC_FP32, seed=6)
-        lp, sw, acc = zeros(8), zeros(8, torch.int64), zeros((8, 8))
+        lp, sw, acc = zeros(8), zeros(8, torch.int64), zeros((8, q.NACC))
         q.qmc_sweep(R.d, o, R.pos, lp, sw, 3, 2, 0, acc)
         torch.cuda.synchronize()
         if shape == t:
@@ -156,7 +156,7 @@ def test_full_size_sampled_walkers():
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     q.qmc_init_walkers(d, 0x5EED0003, 0.1, opt, pos)
     start = pos.cpu().numpy().astype(np.float64)
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(d, opt, pos, lp)
     q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0003, 1, 1, acc)
     assert q.qmc_status(timeout_ms=300000) == 0
@@ -187,8 +187,8 @@ def test_persistent_queue_mode_matches_oracle_and_static_path():
     A = lattice_batch(ns, q.QMC_FP64, seed=8)
     B = lattice_batch(ns, q.QMC_FP64, seed=8)
     opt = q.options(precision=q.QMC_FP64, recompute_every=3)
-    la, sa, aa = zeros(W), zeros(W, torch.int64), zeros((W, 8))
-    lb, sb, ab = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    la, sa, aa = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
+    lb, sb, ab = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(A.d, opt, A.pos, la)
     q.qmc_log_psi(B.d, opt, B.pos, lb)
     q.qmc_sweep(A.d, opt, A.pos, la, sa, 0xD1CE, 4, 2, aa)
@@ -216,8 +216,8 @@ def test_uneven_batch_with_a_dominant_walker():
     A = lattice_batch(ns, q.QMC_FP64, seed=9)
     B = lattice_batch(ns, q.QMC_FP64, seed=9)
     opt = q.options(precision=q.QMC_FP64, recompute_every=2)
-    la, sa, aa = zeros(W), zeros(W, torch.int64), zeros((W, 8))
-    lb, sb, ab = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    la, sa, aa = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
+    lb, sb, ab = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(A.d, opt, A.pos, la)
     q.qmc_log_psi(B.d, opt, B.pos, lb)
     q.qmc_sweep(A.d, opt, A.pos, la, sa, 0xB16, 3, 1, aa)
@@ -245,7 +245,7 @@ def test_mixed_sweep_matches_oracle_and_energy_pass(tpw):
     opt = q.options(precision=q.QMC_FP32, recompute_every=0, threads_per_walker=tpw)
     lp = zeros(W)
     q.qmc_log_psi(P.d, opt, P.pos, lp)
-    sw, acc = zeros(W, torch.int64), zeros((W, 8))
+    sw, acc = zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_sweep(P.d, opt, P.pos, lp, sw, 0x313, 2, 2, acc)
     e = zeros((W, 5))
     q.qmc_local_energy(P.d, q.options(precision=q.QMC_FP32), P.pos, e)
@@ -272,7 +272,7 @@ def test_persistent_queue_mode_survives_a_faulted_walker():
     before = P.pos.clone()
     bad = P.d[3]
     P.pos[bad.offset + 7] = float("nan")
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_sweep(P.d, q.options(), P.pos, lp, sw, 4, 6, 3, acc)
     with pytest.raises(q.QmcError, match="bad coordinate"):
         q.qmc_status(timeout_ms=120000)

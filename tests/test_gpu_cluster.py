@@ -24,7 +24,7 @@ def test_cluster_sweep_matches_oracle(n, W, proposal):
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     q.qmc_init_walkers(d, 0xC1, 0.1, opt, pos)
     start = pos.cpu().numpy()
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(d, opt, pos, lp)
     launches = q.qmc_launch_count()
     q.qmc_sweep(d, opt, pos, lp, sw, 0xC1, 2, 0, acc)

@@ -39,7 +39,7 @@ def test_sweep_energy_with_drift_scratch_matches_the_pass():
     opt = q.options(precision=q.QMC_FP32, recompute_every=1, threads_per_walker=128)
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     q.qmc_init_walkers(d, 12, 0.1, opt, pos)
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(d, opt, pos, lp)
     q.qmc_sweep(d, opt, pos, lp, sw, 12, 2, 2, acc)
     e = zeros((W, 5))

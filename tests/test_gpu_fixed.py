@@ -120,7 +120,7 @@ def test_padding_is_ignored_and_left_alone():
     out = zeros((P.W, 5))
     q.qmc_local_energy(P.d, q.options(), P.pos, out)
     assert torch.isfinite(out).all()
-    lp, sw, acc = zeros(P.W), zeros(P.W, torch.int64), zeros((P.W, 8))
+    lp, sw, acc = zeros(P.W), zeros(P.W, torch.int64), zeros((P.W, q.NACC))
     q.qmc_sweep(P.d, q.options(), P.pos, lp, sw, 1, 2, 1, acc)
     assert q.qmc_status(timeout_ms=60000) == 0
     assert np.all(np.isnan(P.padding(0))) and np.all(np.isnan(P.padding(1)))
@@ -145,7 +145,7 @@ def test_nonfinite_coordinates_are_flagged_not_faulted():
     before = P.pos.clone()
     r = P.d[1]
     P.pos[r.offset + 5] = float("nan")
-    lp, sw, acc = zeros(P.W), zeros(P.W, torch.int64), zeros((P.W, 8))
+    lp, sw, acc = zeros(P.W), zeros(P.W, torch.int64), zeros((P.W, q.NACC))
     q.qmc_sweep(P.d, q.options(), P.pos, lp, sw, 3, 2, 0, acc)
     with pytest.raises(q.QmcError, match="DEVICE"):
         q.qmc_status(timeout_ms=60000)
@@ -205,7 +205,7 @@ def test_pair_correlation_of_a_liquid():
     opt = q.options()
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     q.qmc_init_walkers(d, 21, 0.1, opt, pos)
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_sweep(d, opt, pos, lp, sw, 21, 300, 0, acc)
     nbins, rmax = 70, L / 2
     hist = zeros((W, nbins), torch.int64)

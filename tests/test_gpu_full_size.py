@@ -52,7 +52,7 @@ def test_uneven_batch_sampled_walkers():
     q.qmc_init_walkers(d, 0x5EED0004, 0.1, opt, pos)
     q.qmc_autotune(d, opt, pos)
     start = pos.cpu().numpy()
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(d, opt, pos, lp)
     q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0004, 1, 1, acc)
     assert q.qmc_status(timeout_ms=300000) == 0
@@ -78,7 +78,7 @@ def test_large_walkers_sampled_with_adjoint():
     q.qmc_init_walkers(d, 0x5EED0005, 0.1, opt, pos)
     q.qmc_autotune(d, opt, pos)
     start = pos.cpu().numpy()
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(d, opt, pos, lp)
     q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0005, 1, 1, acc)
     grad = zeros((W, 6))
@@ -107,7 +107,7 @@ def test_fp64_batch_sampled_walkers_bit_for_bit():
     pos = torch.empty(W * 3 * pad, dtype=torch.float64, device="cuda")
     q.qmc_init_walkers(d, 0x5EED0002, 0.1, opt, pos)
     start = pos.cpu().numpy()
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(d, opt, pos, lp)
     q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0002, 3, 3, acc)
     assert q.qmc_status(timeout_ms=300000) == 0

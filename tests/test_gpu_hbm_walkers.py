@@ -39,7 +39,7 @@ def test_walker_beyond_shared_memory():
     opt = q.options(precision=q.QMC_FP32, recompute_every=1)
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     q.qmc_init_walkers(d, 11, 0.1, opt, pos)
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(d, opt, pos, lp)
     lp0 = lp.clone()
     q.qmc_sweep(d, opt, pos, lp, sw, 11, 1, 1, acc)

@@ -33,7 +33,7 @@ def _batch(n, W, precision, step, proposal=q.QMC_CUBE, b=qi.B_HE, seed=1, id0=0)
     dt = torch.float64 if precision == q.QMC_FP64 else torch.float32
     pos = torch.empty(W * 3 * pad, dtype=dt, device="cuda")
     q.qmc_init_walkers(d, seed, 0.1, opt, pos)
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(d, opt, pos, lp)
     return d, opt, pos, lp, sw, acc
 

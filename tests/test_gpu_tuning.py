@@ -24,7 +24,7 @@ def test_tuned_step_gives_the_target_acceptance(proposal):
     opt = q.options(precision=q.QMC_FP32, proposal=proposal)
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     q.qmc_init_walkers(descs_of(0.5), seed, 0.1, opt, pos)
-    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, 8))
+    lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(descs_of(0.5), opt, pos, lp)
     q.qmc_sweep(descs_of(0.5), opt, pos, lp, sw, seed, 20, 0, acc)  # equilibration
     step, rates = tuning.tune_step(descs_of, opt, pos, lp, sw, seed, acc, target=0.5, probes=8)

@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _state(P):
-    return zeros(P.W), zeros(P.W, torch.int64), zeros((P.W, 8))
+    return zeros(P.W), zeros(P.W, torch.int64), zeros((P.W, q.NACC))
 
 
 @pytest.mark.parametrize("prec", [q.QMC_FP32, q.QMC_FP64])
@@ -70,7 +70,7 @@ def test_static_sweep_rejects_too_many_walkers():
     rows = [(n, n, w * 3 * n, w, 10.0, 0.0, 3.0, 5.0, 0.5) for w in range(q.QMC_STATIC_MAX_WALKERS + 1)]
     d = q.descs(rows)
     pos = zeros(len(rows) * 3 * n, torch.float32)
-    lp, sw, acc = zeros(len(rows)), zeros(len(rows), torch.int64), zeros((len(rows), 8))
+    lp, sw, acc = zeros(len(rows)), zeros(len(rows), torch.int64), zeros((len(rows), q.NACC))
     with pytest.raises(q.QmcError, match="at most 4096 walkers"):
         q.qmc_sweep_static(d, q.options(), pos, lp, sw, 1, 1, 0, acc)
     assert q.lib().qmc_sweep_static(d, len(rows), C.byref(q.options()), C.c_void_p(pos.data_ptr()),
