@@ -235,6 +235,8 @@ def run_native(args):
     torch.cuda.synchronize()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    # measured arithmetic rates of this GPU (per clock per SM), outside the timed region
+    probe = q.qmc_probe_rates(4, 256, 2000)
 
     def one_step():
         q.qmc_sweep(d, opt, pos, logpsi, sweeps, seed, SWEEPS_PER_STEP, SWEEPS_PER_STEP, accum, stream)
@@ -269,6 +271,20 @@ def run_native(args):
         total_ms = t.item()
         dist.barrier()
     stats = replicas.block_stats(accum, n)
+
+    # ---- the energy pass on its own: the same step without the energy sample (untimed by the
+    # bench line; the chains advance as in any step) ----
+    noe = []
+    for _ in range(3):
+        flush.zero_()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        q.qmc_sweep(d, opt, pos, logpsi, sweeps, seed, SWEEPS_PER_STEP, 0, accum, stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        noe.append(a_.elapsed_time(b_))
+    accum.zero_()
+    energy_ms = max(total_ms / args.steps - float(np.median(noe)), 1e-6)
 
     pe_step = pair_evals_per_sweep(n) * W * SWEEPS_PER_STEP
     value = pe_step * world * args.steps / (total_ms * 1e-3)
@@ -337,6 +353,7 @@ def run_native(args):
     # ---- roofline of the dominant kernel (the sweep kernel: one launch per step) ----
     peaks = _peaks()
     clk = clock.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    energy_ops = energy_pairs * C_ENERGY / (energy_ms * 1e-3) / 1e12
     peak_tops = nsm * FP32_LANES_PER_SM * clk * 1e6 / 1e12
     # the SFU (MUFU) co-limit: rsqrt and rcp per pair evaluation; rsqrt, rcp and ex2 per energy pair
     # (the damping exponential, taken only where a lane needs it, is not counted)
@@ -384,6 +401,14 @@ def run_native(args):
             "e2e": {"value": pe_step * world / (e2e_ms * 1e-3), "unit": "pair evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "copy_ms_per_step": copy_ms},
             "gpu_launches": launches,
+            "energy_pass": {"ms_per_sample": energy_ms, "pairs_per_s": energy_pairs * world / (energy_ms * 1e-3),
+                            "achieved_tops": energy_ops, "frac": energy_ops / peak_tops,
+                            "how": "step time minus the median of 3 steps without the energy sample"},
+            "probe": {"per_clock_per_sm": probe, "how": "qmc_probe_rates(4 CTAs/SM, 256 threads, 2000 iters)",
+                      "pair_evals_per_clock_per_sm_achieved": value / world / (nsm * clk * 1e6),
+                      "pair_evals_ceiling_of_probe": probe["pair_evals"],
+                      "ffma2_peak_tops": probe["ffma2"] * nsm * clk * 1e6 / 1e12,
+                      "frac_of_probed_ffma2": achieved / (probe["ffma2"] * nsm * clk * 1e6 / 1e12)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
                          "frac": achieved / peak_tops, "traffic": traffic,
                          "note": f"FP32-pipe lane ops ({C_PAIR:g}/pair eval, {C_ENERGY:g}/energy pair) vs "
@@ -475,7 +500,7 @@ def run_uneven(args):
 
 
 def run_large(args):
-    """N = --large-n (default 10000; 40960 is the paper's largest system, Sec. 7.4) at
+    """N = --large-n (default 10000; 40960 is the paper's largest system, Sec. 7.5) at
     0.02186 A^-3, one walker per SM, FP32; a step = --large-sweeps sweeps (default 20) then the adjoint (ln psi, E_L and
     their (b, m) derivatives) of every walker.  Walkers beyond one CTA's shared memory run from
     HBM (L2-resident at these sizes)."""
@@ -488,7 +513,7 @@ def run_large(args):
     pad = qi.pad4(n)
     d = q.descs([(n, pad, w * 3 * pad, w, L, 0.0, qi.B_HE, 5.0, 0.8) for w in range(W)])
     # --large-plain: macroupdates only (no energy samples, no ln psi recomputes), the paper's
-    # measure of Sec. 7.4; with few walkers this runs each walker on a thread-block cluster
+    # measure of Sec. 7.5; with few walkers this runs each walker on a thread-block cluster
     opt = q.options(precision=q.QMC_FP32, recompute_every=0 if args.large_plain else 50)
     E = 0 if args.large_plain else S
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
@@ -696,9 +721,19 @@ def run_t2e(args):
 def run_c3(args):
     """The paper-sized statistics run: N = 1952 at 0.02186 A^-3, 528 walkers in FP32 (the bench
     workload: cube step bisected to about 50 % acceptance), 200 equilibration + 5000 measured
-    sweeps, E_L every 5, 50 blocks of 100 sweeps averaged in FP64; beside it the same chains in FP64
-    on the first 152 walkers (one per SM), 200 + --c3-fp64-sweeps measured sweeps (the full FP64
-    run would take about half an hour).  E/N of both with their errors and the combined 2 sigma."""
+    sweeps, E_L every 5, 50 blocks of 100 sweeps averaged in FP64.
+
+    Then the same 528 chains in FP64 beside FP32, paired on the same Philox streams: from the
+    FP32 run's final state the FP64 chains relax for --c3-pair-equil sweeps; then, for
+    --c3-pair-sweeps sweeps in segments of --c3-segment, each segment starts the FP32 chains from
+    the FP64 chains' state (coordinates rounded to FP32, the same ln psi, sweep counters and
+    random numbers) and both run the segment with E_L every sweep.  While the decisions agree
+    the two chains hold the same configurations, so the paired difference of each energy per
+    atom measures the error the FP32 path adds -- its estimator error and the sampling bias of
+    the decisions that differ (near ties), which relaxes within a few sweeps (the energy's
+    autocorrelation time is about one sweep) -- with a far smaller error bar than two
+    independent runs.  The FP64 chains alone are also an FP64 run of all 528 walkers, compared
+    with the 5000-sweep FP32 run by the combined 2 sigma."""
     import torch
     import paper_1312_1282_gb300 as q
     from paper_1312_1282_gb300 import tuning
@@ -711,15 +746,12 @@ def run_c3(args):
     def descs(step, walkers):
         return q.descs([(n, pad, w * 3 * pad, w, L, 0.0, qi.B_HE, 5.0, step) for w in range(walkers)])
 
-    def state(prec, walkers):
-        dt = torch.float64 if prec == q.QMC_FP64 else torch.float32
-        return (torch.empty(walkers * 3 * pad, dtype=dt, device="cuda"),
-                torch.zeros(walkers, dtype=torch.float64, device="cuda"),
-                torch.zeros(walkers, dtype=torch.int64, device="cuda"),
-                torch.zeros(walkers, q.NACC, dtype=torch.float64, device="cuda"))
+    def zeros(*shape, dtype=torch.float64):
+        return torch.zeros(*shape, dtype=dtype, device="cuda")
 
     opt = q.options(precision=q.QMC_FP32, recompute_every=50)
-    pos, lp, sw, acc = state(q.QMC_FP32, W)
+    pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
+    lp, sw, acc = zeros(W), zeros(W, dtype=torch.int64), zeros(W, q.NACC)
     q.qmc_init_walkers(descs(0.8, W), seed, 0.1, opt, pos)
     q.qmc_log_psi(descs(0.8, W), opt, pos, lp)
     # step bisection on 4-sweep probes of the chains (as in the headline run)
@@ -729,42 +761,153 @@ def run_c3(args):
     t0 = time.time()
     q.qmc_sweep(d, opt, pos, lp, sw, seed, 200, 0, acc)
     blocks = []
-    walker_sum = torch.zeros(W, dtype=torch.float64, device="cuda")
+    walker_sum = zeros(W)
+    drift_max = 0.0
     for _ in range(50):
         acc.zero_()
         q.qmc_sweep(d, opt, pos, lp, sw, seed, 100, 5, acc)
         e = acc[:, 0] / acc[:, 6] / n
         walker_sum += e
         blocks.append(float(e.mean()))
+        drift_max = max(drift_max, float(acc[:, 9].max()))
     torch.cuda.synchronize()
     t32 = time.time() - t0
     assert q.qmc_status(None, 600000) == 0
     b = np.array(blocks)
     wm = (walker_sum / 50).cpu().numpy()
     fp32 = {"E": float(b.mean()), "err_blocks": float(b.std(ddof=1) / math.sqrt(len(b))),
-            "err_walkers": float(wm.std(ddof=1) / math.sqrt(W)), "walkers": W, "sweeps": 5000, "seconds": t32}
+            "err_walkers": float(wm.std(ddof=1) / math.sqrt(W)), "walkers": W, "sweeps": 5000, "seconds": t32,
+            "logpsi_drift_max": drift_max}
 
-    W64 = min(W, torch.cuda.get_device_properties(0).multi_processor_count)
+    # ---- FP64 beside FP32 on the same streams, paired segment by segment ----
     opt64 = q.options(precision=q.QMC_FP64, recompute_every=50)
-    pos64, lp64, sw64, acc64 = state(q.QMC_FP64, W64)
-    d64 = descs(step, W64)
-    q.qmc_init_walkers(d64, seed, 0.1, opt64, pos64)
-    q.qmc_log_psi(d64, opt64, pos64, lp64)
+    pos64, lp64, sw64, acc64 = pos.double(), zeros(W), sw.clone(), zeros(W, q.NACC)
+    q.qmc_log_psi(d, opt64, pos64, lp64)
     t0 = time.time()
-    q.qmc_sweep(d64, opt64, pos64, lp64, sw64, seed, 200, 0, acc64)
-    acc64.zero_()
-    q.qmc_sweep(d64, opt64, pos64, lp64, sw64, seed, args.c3_fp64_sweeps, 5, acc64)
+    q.qmc_sweep(d, opt64, pos64, lp64, sw64, seed, args.c3_pair_equil, 0, acc64)
+    seg = args.c3_segment
+    nseg = max(1, args.c3_pair_sweeps // seg)
+    cols = [0, 2, 3, 4, 5]  # E_L, V, T_L, T_PB, T_F
+    e32 = np.zeros((nseg, W, 5))
+    e64 = np.zeros((nseg, W, 5))
+    coupled = np.zeros((nseg, W), dtype=bool)
+    for k in range(nseg):
+        pos.copy_(pos64)
+        lp.copy_(lp64)
+        sw.copy_(sw64)
+        acc.zero_()
+        acc64.zero_()
+        q.qmc_sweep(d, opt, pos, lp, sw, seed, seg, 1, acc)
+        q.qmc_sweep(d, opt64, pos64, lp64, sw64, seed, seg, 1, acc64)
+        a32, a64 = acc.cpu().numpy(), acc64.cpu().numpy()
+        e32[k] = a32[:, cols] / a32[:, 6:7] / n
+        e64[k] = a64[:, cols] / a64[:, 6:7] / n
+        gap = (pos.double() - pos64).abs().view(W, 3 * pad).max(dim=1).values.cpu().numpy()
+        coupled[k] = (gap < 1e-3) & (a32[:, 7] == a64[:, 7])
     torch.cuda.synchronize()
     t64 = time.time() - t0
     assert q.qmc_status(None, 600000) == 0
-    e64 = (acc64[:, 0] / acc64[:, 6] / n).cpu().numpy()
-    fp64 = {"E": float(e64.mean()), "err_walkers": float(e64.std(ddof=1) / math.sqrt(W64)), "walkers": W64,
-            "sweeps": args.c3_fp64_sweeps, "seconds": t64}
+    diff = (e32 - e64).mean(axis=0)  # per walker, K per atom
+    names = ["E", "V", "T_L", "T_PB", "T_F"]
+    paired = {nm: {"diff_mK": 1e3 * float(diff[:, i].mean()),
+                   "err_mK": 1e3 * float(diff[:, i].std(ddof=1) / math.sqrt(W))} for i, nm in enumerate(names)}
+    w64 = e64.mean(axis=0)
+    fp64 = {"E": float(w64[:, 0].mean()), "err_walkers": float(w64[:, 0].std(ddof=1) / math.sqrt(W)), "walkers": W,
+            "sweeps": nseg * seg, "equilibration_sweeps": args.c3_pair_equil, "seconds": t64,
+            "segments": nseg, "segment_sweeps": seg, "coupled_segments": float(coupled.mean())}
     err32 = max(fp32["err_blocks"], fp32["err_walkers"])
-    res = {"config": "N=1952, 528 walkers FP32: 200 + 5000 sweeps, E_L every 5, 50 blocks; FP64 on 152 walkers",
-           "step_A": step, "fp32": fp32, "fp64": fp64, "diff_mK": 1e3 * (fp32["E"] - fp64["E"]),
+    res = {"config": "N=1952, 528 walkers FP32: 200 + 5000 sweeps, E_L every 5, 50 blocks; then FP32 and FP64 "
+                     "chains of all 528 walkers paired on the same streams",
+           "step_A": step, "fp32": fp32, "fp64": fp64, "paired_fp32_minus_fp64": paired,
+           "diff_unpaired_mK": 1e3 * (fp32["E"] - fp64["E"]),
            "combined_2sigma_mK": 2e3 * math.hypot(err32, fp64["err_walkers"])}
     print(json.dumps(res), flush=True)
+    return 0
+
+
+def run_mask(args):
+    """Load masking (Sec. 4.2 and the experiment of Sec. 7.1, Fig. 5) on one GPU: a fixed number S
+    of macroupdates with an analysis (local energy and g(r) histogram of every walker) every m
+    macroupdates, for several m, in the sequential schedule (one stream) and the masked one (the
+    analyses on a second stream, on snapshots, overlapped with the next macroupdates).  Two
+    workloads: the paper's demonstration shape (N = 512, 8 walkers, one CTA each) and its largest
+    system (N = 40 960, 13 walkers, a thread-block cluster each, leaving SMs idle).  Beside the
+    measured totals: t_G and t_A measured alone, the totals Eqs. (serialtime) and (maskedtime)
+    predict from them, and least-squares fits a + b / m as in the paper."""
+    import torch
+    import paper_1312_1282_gb300 as q
+    from paper_1312_1282_gb300 import masking
+    torch.cuda.set_device(0)
+    cases = [("paper demo: N=512, 8 walkers", 512, 8, 480, (1, 2, 4, 8, 16, 32)),
+             ("largest system: N=40960, 13 walkers on clusters", 40960, 13, args.mask_large_sweeps, (1, 2, 4, 8, 16))]
+    out = []
+    for name, n, W, S, ms in cases:
+        L = qi.box_side(n, qi.RHO_HE)
+        pad = qi.pad4(n)
+        d = q.descs([(n, pad, w * 3 * pad, w, L, 0.0, qi.B_HE, 5.0, 0.8) for w in range(W)])
+        opt = q.options(precision=q.QMC_FP32, recompute_every=0)
+        pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
+        q.qmc_init_walkers(d, 0x5EED0007, 0.1, opt, pos)
+        lp = torch.zeros(W, dtype=torch.float64, device="cuda")
+        sw = torch.zeros(W, dtype=torch.int64, device="cuda")
+        acc = torch.zeros(W, q.NACC, dtype=torch.float64, device="cuda")
+        q.qmc_log_psi(d, opt, pos, lp)
+        q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0007, 4, 0, acc)  # warm
+        nbins = 200
+        hist = torch.zeros(W, nbins, dtype=torch.int64, device="cuda")
+        en = torch.zeros(max(S // min(ms), 1), W, 5, dtype=torch.float64, device="cuda")
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0
+
+        reps = 4 if n <= 4096 else 1
+        t_G = timed(lambda: q.qmc_sweep(d, opt, pos, lp, sw, 0x5EED0007, S, 0, acc)) / S
+        t_A = min(timed(lambda: (q.qmc_local_energy(d, opt, pos, en[0]),
+                                 q.qmc_pair_hist(d, opt, pos, nbins, L / 2, hist))) for _ in range(reps))
+        rows = []
+        for m in ms:
+            row = {"m": m, "analyses": S // m}
+            for masked in (False, True):
+                row["masked" if masked else "sequential"] = min(timed(lambda: masking.run_schedule(
+                    d, opt, pos, lp, sw, acc, 0x5EED0007, m, S // m, energies=en, hist=hist, nbins=nbins, rmax=L / 2,
+                    masked=masked)) for _ in range(reps))
+            row["model_sequential"] = S * t_G + S // m * t_A
+            row["model_masked"] = S // m * max(m * t_G, t_A)
+            rows.append(row)
+        assert q.qmc_status(None, 600000) == 0
+        inv = np.array([1.0 / r["m"] for r in rows])
+        fits = {}
+        for key in ("sequential", "masked"):
+            b, a = np.polyfit(inv, np.array([r[key] for r in rows]), 1)
+            fits[key] = {"a": a, "b": b}
+        alpha = t_A / t_G
+        res = {"config": "load masking: " + name, "macroupdates": S, "t_G_ms": 1e3 * t_G, "t_A_ms": 1e3 * t_A,
+               "alpha": alpha, "m_eq_optimalGPU": alpha, "rows": rows, "fit_a_plus_b_over_m": fits}
+        print(json.dumps(res), flush=True)
+        out.append(res)
+        del pos, hist, en
+    return 0
+
+
+def run_pipes(args):
+    """The arithmetic rates that bound the sweep, measured on this GPU by qmc_probe_rates (per
+    clock per SM): FP32 FMA scalar and packed, FP32 min, SFU rsqrt, FP64 FMA, and the pair
+    evaluations of the sweep's partner arithmetic alone, at several launch shapes."""
+    import torch
+    import paper_1312_1282_gb300 as q
+    torch.cuda.set_device(0)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    rows = []
+    for bps, thr in ((2, 128), (4, 128), (4, 256), (2, 512), (1, 1024), (8, 128), (3, 512)):
+        q.qmc_probe_rates(bps, thr, 200)  # warm
+        rows.append({"ctas_per_sm": bps, "threads": thr, "warps_per_sm": bps * thr // 32,
+                     **q.qmc_probe_rates(bps, thr, 4000)})
+    print(json.dumps({"config": "arithmetic rates per clock per SM (qmc_probe_rates)", "sms": nsm, "rows": rows}),
+          flush=True)
     return 0
 
 
@@ -794,13 +937,17 @@ def main():
     ap.add_argument("--tpw", type=int, default=0, help="threads per walker of the headline run (0: autotune)")
     ap.add_argument("--groups", type=int, default=0, help="walkers per CTA with --tpw (default 1)")
     ap.add_argument("--large-n", type=int, default=10000, help="large: atoms per walker")
-    ap.add_argument("--c3-fp64-sweeps", type=int, default=600, help="c3: measured FP64 sweeps")
+    ap.add_argument("--c3-pair-sweeps", type=int, default=600, help="c3: paired FP32/FP64 sweeps")
+    ap.add_argument("--c3-pair-equil", type=int, default=20, help="c3: FP64 relaxation sweeps before pairing")
+    ap.add_argument("--c3-segment", type=int, default=50, help="c3: sweeps per paired segment")
     ap.add_argument("--large-sweeps", type=int, default=20, help="large: sweeps per step")
     ap.add_argument("--large-walkers", type=int, default=0, help="large: walkers (0: one per SM)")
     ap.add_argument("--large-plain", action="store_true", help="large: sweeps only (no energy, no ln psi recompute)")
+    ap.add_argument("--mask-large-sweeps", type=int, default=32, help="mask: macroupdates of the N=40960 case")
     ap.add_argument("--t2e-seconds", type=float, default=3.0, help="t2e: production seconds per N and m")
     ap.add_argument("--t2e-sizes", default="", help="t2e: comma-separated N (default 128..4000)")
-    ap.add_argument("--config", default="headline", choices=["headline", "uneven", "large", "fp64cmp", "t2e", "c3"],
+    ap.add_argument("--config", default="headline",
+                    choices=["headline", "uneven", "large", "fp64cmp", "t2e", "c3", "pipes", "mask"],
                     help="headline: the benchmark line; the others measure the other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -817,6 +964,10 @@ def main():
         return run_t2e(args)
     if args.config == "c3":
         return run_c3(args)
+    if args.config == "pipes":
+        return run_pipes(args)
+    if args.config == "mask":
+        return run_mask(args)
     return run_native(args)
 
 

@@ -189,7 +189,7 @@ int qmc_pair_hist(const qmc_walker_desc *d, int W, const qmc_options *opt, const
 
 /*
  * qmc_autotune -- the launch shape of qmc_sweep chosen by measurement (the paper's heuristics of
- * Sec. 4.3 -- as many resident blocks as fit, fewer threads than atoms, multiples of 32 -- are
+ * Sec. 4.4 -- as many resident blocks as fit, fewer threads than atoms, multiples of 32 -- are
  * the search space): qmc_sweep is timed on a scratch copy of `pos` for every admissible pair
  * (threads per walker, walkers per CTA) -- threads 32 .. 1024 in powers of two, at most one
  * thread per 4-atom partner chunk; walkers per CTA 1, 2, 4, 8 with at most 256 threads and the

@@ -74,6 +74,7 @@ def lib():
             L.orc_aziz.argtypes = [C.c_double]
             L.orc_aziz.restype = C.c_double
             L.orc_pair_u.argtypes = [C.c_double] * 4 + [C.c_int, _D]
+            L.orc_pair_u_many.argtypes = [C.c_int, _D] + [C.c_double] * 3 + [C.c_int, _D]
             geom = [C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int]
             L.orc_log_psi.argtypes = geom
             L.orc_log_psi.restype = C.c_double
@@ -130,6 +131,14 @@ def pair_u(r, L, b, m=5.0, sym=1):
     o = np.zeros(9)
     lib().orc_pair_u(float(r), float(L), float(b), float(m), int(sym), _dp(o))
     return o
+
+
+def pair_u_many(r, L, b, m=5.0, sym=1):
+    """pair_u at every distance of the array r: shape r.shape + (9,)."""
+    rr = np.ascontiguousarray(r, dtype=np.float64).ravel()
+    o = np.zeros((rr.size, 9))
+    lib().orc_pair_u_many(rr.size, _dp(rr), float(L), float(b), float(m), int(sym), _dp(o))
+    return o.reshape(np.shape(r) + (9,))
 
 
 def log_psi(pos, L, b, m=5.0, sym=1) -> float:

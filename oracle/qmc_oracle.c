@@ -175,6 +175,12 @@ ORC_API void orc_pair_u(double r, double L, double b, double m, int sym, double 
     out[6] = p.um; out[7] = p.u1m; out[8] = p.u2m;
 }
 
+/* orc_pair_u at each of cnt distances r[k]: out[9 k .. 9 k + 8] (test scales need many pairs). */
+ORC_API void orc_pair_u_many(int cnt, const double *r, double L, double b, double m, int sym, double *out)
+{
+    for (int k = 0; k < cnt; ++k) orc_pair_u(r[k], L, b, m, sym, out + 9 * (size_t)k);
+}
+
 /* HFD-B(HE) ("Aziz II") pair potential in K, r in A, without cutoff. */
 ORC_API double orc_aziz(double r)
 {

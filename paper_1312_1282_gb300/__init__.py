@@ -22,7 +22,8 @@ from . import build as _build
 __all__ = [
     "QMC_FP32", "QMC_FP64", "QMC_CUBE", "QMC_GAUSS", "QmcError", "WalkerDesc", "Options", "lib", "descs",
     "options", "qmc_init_walkers", "qmc_sweep", "qmc_local_energy", "qmc_energy_grad", "qmc_log_psi",
-    "qmc_trial_delta", "qmc_pair_hist", "pair_correlation", "qmc_sweep_static", "QMC_STATIC_MAX_WALKERS", "qmc_autotune", "qmc_capacity", "qmc_status", "qmc_launch_count", "qmc_version",
+    "qmc_trial_delta", "qmc_pair_hist", "pair_correlation", "qmc_sweep_static", "QMC_STATIC_MAX_WALKERS", "qmc_autotune",
+    "qmc_probe_rates", "PROBE_FIELDS", "qmc_capacity", "qmc_status", "qmc_launch_count", "qmc_version",
     "qmc_shutdown", "Batch", "QmcGrad", "ACCUM_FIELDS", "NACC", "ENERGY_FIELDS", "GRAD_FIELDS",
 ]
 
@@ -84,6 +85,7 @@ def lib():
         L.qmc_pair_hist.argtypes = [D, C.c_int, O, _VP, C.c_int, C.c_double, _VP, _VP]
         L.qmc_sweep_static.argtypes = [D, C.c_int, O, _VP, _VP, _VP, C.c_uint64, C.c_int, C.c_int, _VP, _VP, _VP]
         L.qmc_capacity.argtypes = [C.c_int]
+        L.qmc_probe_rates.argtypes = [C.c_int, C.c_int, C.c_int, _DP, _VP]
         L.qmc_status.argtypes = [_VP, C.c_int, C.POINTER(C.c_uint32)]
         L.qmc_launch_count.restype = C.c_uint64
         L.qmc_last_error.restype = C.c_char_p
@@ -222,6 +224,18 @@ def qmc_autotune(d, opt, pos, stream=None) -> tuple[int, int]:
     t, g = C.c_int(0), C.c_int(0)
     _check(lib().qmc_autotune(d, len(d), C.byref(opt), _ptr(pos), _stream(stream), C.byref(t), C.byref(g)))
     return t.value, g.value
+
+
+PROBE_FIELDS = ("ffma", "ffma2", "fmnmx", "rsqrt", "dfma", "pair_evals")
+
+
+def qmc_probe_rates(blocks_per_sm=4, threads=256, iters=2000, stream=None) -> dict:
+    """Measured rates per clock per SM on the current GPU (include/qmc_probe.h): lane operations
+    of FP32 FMA (scalar, packed), FP32 min, SFU rsqrt, FP64 FMA, and pair evaluations of the
+    sweep's partner arithmetic alone."""
+    out = (C.c_double * len(PROBE_FIELDS))()
+    _check(lib().qmc_probe_rates(blocks_per_sm, threads, iters, out, _stream(stream)))
+    return dict(zip(PROBE_FIELDS, list(out)))
 
 
 def qmc_capacity(precision) -> int:

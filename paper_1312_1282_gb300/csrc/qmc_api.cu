@@ -89,9 +89,10 @@ std::unordered_map<uint64_t, Tuned> g_tuned;  // shape key -> autotuned launch s
 
 // Failure tests only (the library's own tests run them in child processes): QMC_WAIT_LIMIT_MS
 // shortens the limit of every bounded device wait (default 10 s); QMC_TEST_DROP=queue makes the
-// persistent sweep never push back the first walker of its order after its first chunk, and
-// QMC_TEST_DROP=cluster makes CTA rank 1 of the first walker's cluster never take part in an
-// exchange -- so that waits run out and QMC_DEVERR_TIMEOUT is raised without any fault.
+// first persistent sweep of the process never push back the first walker of its order after its
+// first chunk, and QMC_TEST_DROP=cluster makes CTA rank 1 of the first walker's cluster in the
+// first cluster sweep of the process never take part in an exchange -- so that waits run out and
+// QMC_DEVERR_TIMEOUT is raised without any fault, and later calls run normally.
 struct TestKnobs {
     unsigned long long wait_ns = 10000000000ull;
     int drop_queue = 0, drop_cluster = 0;
@@ -111,6 +112,13 @@ const TestKnobs &knobs()
         return t;
     }();
     return k;
+}
+
+// the one call of the process that withholds a push or an exchange (failure tests only)
+bool take_drop(int wanted)
+{
+    static std::atomic<int> left{1};
+    return wanted && left.exchange(0) == 1;
 }
 
 uint64_t fnv(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
@@ -584,6 +592,7 @@ int mixed_sweep(const qmc_walker_desc *d, int W, const qmc_options *o, const Pla
     small.q_tail = P.q_ctr + 1;
     small.q_slots = P.q_slots;
     small.q_prog = P.q_prog;
+    small.drop_push = take_drop(knobs().drop_queue) ? 1 : 0;
     big.fscr = small.fscr = nullptr;
     const size_t fb = tile_b == 2 ? (size_t)grid * 3 * big.stride : 0;
     const size_t fs = tile_s == 2 ? (size_t)grid * Gs * 3 * small.stride : 0;
@@ -650,7 +659,7 @@ int cluster_sweep(const qmc_walker_desc *d, int W, const qmc_options *o, const P
     a.sequential = o->sequential;
     a.err = p.ds->err;
     a.wait_ns = knobs().wait_ns;
-    a.drop_rank = knobs().drop_cluster ? 1 : -1;
+    a.drop_rank = take_drop(knobs().drop_cluster) ? 1 : -1;
     e = launch_sweep_cluster(W * C, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "cluster sweep launch");
     g_launches.fetch_add(1);
@@ -710,7 +719,7 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     a.q_slots = nullptr;
     a.q_prog = nullptr;
     a.wait_ns = knobs().wait_ns;
-    a.drop_push = knobs().drop_queue;
+    a.drop_push = 0;
     int grid = (W + G - 1) / G;
     const size_t smem = (size_t)G * sh.smem;
     const Variant v = variant_of(P, o);
@@ -766,6 +775,7 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
             a.q_tail = P.q_ctr + 1;
             a.q_slots = P.q_slots;
             a.q_prog = P.q_prog;
+            a.drop_push = take_drop(knobs().drop_queue) ? 1 : 0;
             grid = ctas * p.ds->nsm;
             e = launch_queue_init(P.d_order, W, P.q_slots, P.q_prog, P.q_ctr, P.q_ctr + 1, st);
             if (e != cudaSuccess) return cuda_fail(e, "walker queue init");
@@ -1017,6 +1027,53 @@ int qmc_status(void *stream, int timeout_ms, uint32_t *bits)
                     (h & QMC_DEVERR_NONFINITE_RATIO) ? "[non-finite ratio]" : "",
                     (h & QMC_DEVERR_BAD_INDEX) ? "[atom index out of range]" : "",
                     (h & QMC_DEVERR_TIMEOUT) ? "[a bounded device wait timed out]" : "");
+    return QMC_OK;
+}
+
+int qmc_probe_rates(int blocks_per_sm, int threads, int iters, double *out, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!out) return fail(QMC_ERR_ARG, "out is NULL");
+    if (blocks_per_sm < 1 || blocks_per_sm > 32) return fail(QMC_ERR_ARG, "blocks_per_sm must be in 1..32");
+    if (threads < 32 || threads > 1024 || threads % 32) return fail(QMC_ERR_ARG, "threads must be a multiple of 32 in 32..1024");
+    if (iters < 1 || iters > 1000000) return fail(QMC_ERR_ARG, "iters must be in 1..1000000");
+    int dev, rc;
+    if ((rc = current_device(dev))) return rc;
+    DeviceState *ds;
+    if ((rc = device_state(dev, ds))) return rc;
+    const int nsm = ds->nsm;
+    long long *cycles = nullptr;
+    float *sink = nullptr;
+    cudaError_t e = cudaMalloc(&cycles, sizeof(long long) * (size_t)blocks_per_sm * nsm);
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float) * (size_t)blocks_per_sm * nsm * threads);
+    std::vector<long long> host((size_t)blocks_per_sm * nsm);
+    double res[QMC_PROBE_COUNT] = {};
+    for (int kind = 0; e == cudaSuccess && kind < QMC_PROBE_COUNT; ++kind) {
+        // the pair probe keeps the sweep's register budget: at most 512 threads per CTA
+        const int thr = kind == QMC_PROBE_PAIR ? std::min(threads, 512) : threads;
+        int resident = 0;
+        e = probe_occupancy(kind, thr, &resident);
+        if (e != cudaSuccess) break;
+        resident = std::min(resident, blocks_per_sm);
+        if (resident < 1) {
+            e = cudaErrorInvalidConfiguration;
+            break;
+        }
+        const int grid = resident * nsm;  // every CTA resident at once
+        e = launch_probe(kind, grid, thr, iters, cycles, sink, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), cycles, sizeof(long long) * grid, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        g_launches.fetch_add(1);
+        double mean = 0;
+        for (int b = 0; b < grid; ++b) mean += (double)host[b];
+        mean /= grid;
+        res[kind] = resident * (double)thr * iters * probe_ops_per_thread_iter(kind) / mean;
+    }
+    if (cycles) cudaFree(cycles);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(e, "probe");
+    for (int k = 0; k < QMC_PROBE_COUNT; ++k) out[k] = res[k];
     return QMC_OK;
 }
 

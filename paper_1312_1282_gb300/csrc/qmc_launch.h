@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "qmc_kernels.cuh"
+#include "qmc_probe.h"
 
 namespace qmc {
 
@@ -46,5 +47,11 @@ cudaError_t launch_hist(int precision, int grid, size_t smem, cudaStream_t st, c
                         double rmax, unsigned long long *hist);
 cudaError_t launch_init(int precision, int grid, size_t smem, cudaStream_t st, const DevWalker *walkers,
                         unsigned long long seed, double sigma, void *pos);
+
+// calibration probes (qmc_probe_rates): launcher, resident CTAs per SM, work per thread and loop
+// iteration (lane operations, or pair evaluations for the pair probe)
+cudaError_t launch_probe(int kind, int grid, int threads, int iters, long long *cycles, float *sink, cudaStream_t st);
+cudaError_t probe_occupancy(int kind, int threads, int *blocks);
+double probe_ops_per_thread_iter(int kind);
 
 }  // namespace qmc

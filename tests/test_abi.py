@@ -1,6 +1,7 @@
 """The C-ABI library builds for sm_103a, loads, and exports what include/qmc.h declares
 (CPU only: no compute call is made here)."""
 import ctypes as C
+import glob
 import os
 import re
 import subprocess
@@ -11,12 +12,15 @@ import paper_1312_1282_gb300 as q
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "qmc.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def _declared():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(qmc_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(qmc_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_library_builds_and_loads():
@@ -27,7 +31,7 @@ def test_library_builds_and_loads():
 
 def test_every_declared_symbol_is_exported():
     names = _declared()
-    assert {"qmc_init_walkers", "qmc_sweep", "qmc_local_energy", "qmc_energy_grad"} <= set(names)
+    assert {"qmc_init_walkers", "qmc_sweep", "qmc_local_energy", "qmc_energy_grad", "qmc_probe_rates"} <= set(names)
     lib = C.CDLL(q._build.LIB)
     for nm in names:
         assert hasattr(lib, nm), nm
@@ -73,6 +77,9 @@ def test_host_side_argument_errors_need_no_device():
     with pytest.raises(q.QmcError, match="ARG"):   # misaligned position pointer
         q.qmc_log_psi(d, q.options(), 20, 16, stream=0)
     assert q.lib().qmc_local_energy(d, 0, C.byref(q.options()), C.c_void_p(16), C.c_void_p(16), None) == -1
+    for bad in ((0, 256, 10), (4, 48, 10), (4, 256, 0)):
+        with pytest.raises(q.QmcError, match="ARG"):
+            q.qmc_probe_rates(*bad, stream=0)
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -1,15 +1,16 @@
 """Few walkers of large N run each walker on a thread-block cluster (slices of the walker in the
 shared memory of C CTAs, partial sums exchanged through distributed shared memory).  Chains as
-the oracle's decision by decision except at near ties; ln psi carried through the moves as a
-fresh recompute; ragged slices (N not a multiple of 4 C) and both proposals."""
+the oracle's decision by decision except at near ties, checked sweep by sweep (one sweep per
+call; the oracle reruns each sweep from the GPU's state, and a sweep that differs must contain
+a near tie); ln psi carried through the moves as a fresh recompute; ragged slices (N not a
+multiple of 4 C) and both proposals."""
 import numpy as np
 import pytest
 import torch
 
-import oracle
 import paper_1312_1282_gb300 as q
 import qmc_inputs as qi
-from tests._gpu import H2M, zeros
+from tests._gpu import fp32_sweeps_vs_oracle, zeros
 
 pytestmark = pytest.mark.gpu
 
@@ -26,9 +27,15 @@ def test_cluster_sweep_matches_oracle(n, W, proposal):
     start = pos.cpu().numpy()
     lp, sw, acc = zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))
     q.qmc_log_psi(d, opt, pos, lp)
-    launches = q.qmc_launch_count()
-    q.qmc_sweep(d, opt, pos, lp, sw, 0xC1, 2, 0, acc)
-    assert q.qmc_launch_count() - launches == 1  # one cluster launch, no queue
+    states, accepted, prev = [start], [], np.zeros(W)
+    for _ in range(2):  # one sweep per call
+        launches = q.qmc_launch_count()
+        q.qmc_sweep(d, opt, pos, lp, sw, 0xC1, 1, 0, acc)
+        assert q.qmc_launch_count() - launches == 1  # one cluster launch, no queue
+        states.append(pos.cpu().numpy())
+        a = acc[:, 7].cpu().numpy()
+        accepted.append(a - prev)
+        prev = a
     fresh = zeros(W)
     q.qmc_log_psi(d, opt, pos, fresh)
     assert q.qmc_status(timeout_ms=120000) == 0
@@ -39,13 +46,8 @@ def test_cluster_sweep_matches_oracle(n, W, proposal):
     np.testing.assert_allclose(lp.cpu().numpy(), fresh.cpu().numpy(), rtol=2e-5)
     agree = 0
     for w in range(W):
-        blk0 = start[w * 3 * pad:(w + 1) * 3 * pad].reshape(3, pad)[:, :n].astype(np.float64)
-        blk1 = host[w * 3 * pad:(w + 1) * 3 * pad].reshape(3, pad)[:, :n].astype(np.float64)
-        assert np.all(np.isfinite(blk1)) and np.all((blk1 >= 0) & (blk1 <= L))
-        P = oracle.make_walker(n, L, qi.B_HE, 5.0, step, proposal=proposal, seed=0xC1, wid=w, hbar2_over_m=H2M)
-        opos, _, _, oacc, mg = oracle.run_walker(P, blk0, oracle.log_psi(blk0, L, qi.B_HE), 0, 2, 0, margins=True)
-        if a[w, 7] == oacc[7] and np.abs(blk1 - opos).max() < 1e-3:
-            agree += 1
-        else:
-            assert np.abs(mg).min() < 1e-3, (w, np.abs(mg).min())
-    assert agree >= W - 1
+        blk = [st[w * 3 * pad:(w + 1) * 3 * pad].reshape(3, pad)[:, :n].astype(np.float64) for st in states]
+        assert np.all(np.isfinite(blk[-1])) and np.all((blk[-1] >= 0) & (blk[-1] <= L))
+        agree += fp32_sweeps_vs_oracle(blk, [acc_k[w] for acc_k in accepted], n, L, qi.B_HE, 5.0, step, 0xC1, w,
+                                       proposal=proposal)[0]
+    assert agree >= 2 * W - 1

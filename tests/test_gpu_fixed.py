@@ -1,7 +1,10 @@
 """GPU vs oracle on fixed configurations: local energy, ln psi, (b, m) gradient, trial ratios
 and start configurations, through the C ABI.  FP64: 1e-10 relative; FP32: 1e-5 relative
 (the tolerances of the method's fixed-configuration parity), on batches whose sizes span
-several partner chunks and thread groups with ragged tails."""
+several partner chunks and thread groups with ragged tails.  Quantities that are differences
+(T_L, E_L, the derivatives of E_L, a trial ratio) are compared on the sum of the magnitudes of
+the terms they are made of, computed from the oracle's pair terms; the achieved errors, on that
+scale and on each output's own magnitude, go to the QMC_PARITY_REPORT file when it is set."""
 import math
 
 import numpy as np
@@ -11,7 +14,7 @@ import torch
 import oracle
 import paper_1312_1282_gb300 as q
 import qmc_inputs as qi
-from tests._gpu import H2M, Packed, energy_scale, lattice_batch, zeros
+from tests._gpu import H2M, Packed, energy_scale, grad_scales, lattice_batch, report, trial_scale, zeros
 
 pytestmark = pytest.mark.gpu
 
@@ -24,6 +27,7 @@ def _close(got, want, rel, scale=None):
     scale = np.maximum(np.abs(want), 1e-300) if scale is None else scale
     err = np.abs(np.asarray(got) - np.asarray(want)) / scale
     assert np.all(err <= rel), (err.max(), got, want)
+    return err
 
 
 @pytest.mark.parametrize("prec", PREC)
@@ -34,10 +38,17 @@ def test_local_energy(prec, sym, m):
     out = zeros((P.W, 5))
     q.qmc_local_energy(P.d, opt, P.pos, out)
     got = out.cpu().numpy()
+    worst, worst_own = np.zeros(5), np.zeros(5)
     for w in range(P.W):
         want = oracle.local_energy(P.confs[w], P.Ls[w], P.bs[w], m, sym, H2M)
         # T_L and E_L are differences: compared on the scale of the sums they are built from
-        _close(got[w], want, TOL[prec], energy_scale(want))
+        err = _close(got[w], want, TOL[prec], energy_scale(want))
+        worst = np.maximum(worst, err)
+        if P.confs[w].shape[1] >= 17:  # below that E_L can pass through zero
+            worst_own = np.maximum(worst_own, np.abs(got[w] - want) / np.maximum(np.abs(want), 1e-300))
+    # the achieved error on each output's own magnitude (E_L and T_L included), for the record
+    report("local_energy", prec=prec, sym=sym, m=m, fields="V,T_L,T_PB,T_F,E_L", err_on_summed_scale=worst,
+           err_on_own_magnitude=worst_own)
 
 
 @pytest.mark.parametrize("prec", PREC)
@@ -56,17 +67,17 @@ def test_energy_grad(prec):
     out = zeros((P.W, 6))
     q.qmc_energy_grad(P.d, q.options(precision=prec), P.pos, out)
     got = out.cpu().numpy()
+    worst, worst_own = np.zeros(6), np.zeros(6)
     for w in range(P.W):
         want = oracle.energy_grad(P.confs[w], P.Ls[w], P.bs[w], 5.0, 1, H2M)
-        e = oracle.local_energy(P.confs[w], P.Ls[w], P.bs[w], 5.0, 1, H2M)
-        lap, F = oracle.local_terms(P.confs[w], P.Ls[w], P.bs[w])
-        # derivatives of E_L are sums of kinetic terms with both signs: their scale is the
-        # kinetic magnitude times the derivative's own factor
-        kin = 0.5 * H2M * (np.abs(lap).sum() + (F ** 2).sum())
-        scale = np.array([abs(want[0]), energy_scale(e)[4], abs(want[2]), abs(want[3]) + 1e-300,
-                          kin * 5.0 / P.bs[w] * 2, kin * 4.0])
-        tol = TOL[prec] * (20 if prec == q.QMC_FP32 else 1)
-        _close(got[w], want, tol, np.maximum(scale, 1e-12))
+        # each output on the sum of the magnitudes of the pair terms it is made of (the
+        # derivatives of E_L are sums of kinetic terms of both signs)
+        scale = grad_scales(P.confs[w], P.Ls[w], P.bs[w], 5.0, 1, H2M)
+        err = _close(got[w], want, TOL[prec], np.maximum(scale, 1e-12))
+        worst = np.maximum(worst, err)
+        worst_own = np.maximum(worst_own, np.abs(got[w] - want) / np.maximum(np.abs(want), 1e-300))
+    report("energy_grad", prec=prec, fields="lnpsi,E_L,dlnpsi_db,dlnpsi_dm,dEL_db,dEL_dm", err_on_term_scale=worst,
+           err_on_own_magnitude=worst_own)
 
 
 @pytest.mark.parametrize("prec", PREC)
@@ -81,15 +92,19 @@ def test_trial_delta(prec):
     q.qmc_trial_delta(P.d, q.options(precision=prec), P.pos, torch.tensor(s, device="cuda"),
                       torch.tensor(delta, device="cuda"), M, out)
     got = out.cpu().numpy()
+    worst = 0.0
     for w in range(P.W):
-        lp = oracle.log_psi(P.confs[w], P.Ls[w], P.bs[w])
-        row = 4 * abs(lp) / ns[w] + 1e-3  # typical sum_j |u| of one atom, old + new
         for k in range(M):
             d = delta[w, k]
             if prec == q.QMC_FP32:
                 d = d.astype(np.float32).astype(np.float64)
-            want, _ = oracle.trial_delta(P.confs[w], P.Ls[w], P.bs[w], 5.0, 1, s[w, k], d)
-            assert abs(got[w, k] - want) <= TOL[prec] * row * 10, (w, k, got[w, k], want, row)
+            want, new = oracle.trial_delta(P.confs[w], P.Ls[w], P.bs[w], 5.0, 1, s[w, k], d)
+            # Delta -> 0 cancels: absolute error on sum_j (|u| + |u'|) at the old and new distances
+            scale = trial_scale(P.confs[w], P.Ls[w], P.bs[w], 5.0, 1, s[w, k], new) + 1e-300
+            err = abs(got[w, k] - want) / scale
+            assert err <= TOL[prec], (w, k, got[w, k], want, scale)
+            worst = max(worst, err)
+    report("trial_delta", prec=prec, err_on_term_scale=worst)
 
 
 @pytest.mark.parametrize("prec", PREC)

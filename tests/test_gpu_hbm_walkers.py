@@ -3,7 +3,8 @@
 The HBM path is the same kernels with the coordinates read and written in global memory.  It
 is checked two ways: the whole fixed-configuration and chain parity suites are rerun in a child
 process with QMC_GLOBAL_WALKERS=1 (which forces the HBM path for every batch), and a walker of
-20 000 atoms -- beyond the FP32 shared-memory capacity -- is swept and sampled."""
+20 000 atoms -- beyond the FP32 shared-memory capacity -- is swept and sampled, its energy
+checked against the oracle's."""
 import math
 import os
 import subprocess
@@ -15,7 +16,8 @@ import torch
 
 import paper_1312_1282_gb300 as q
 import qmc_inputs as qi
-from tests._gpu import zeros
+import oracle
+from tests._gpu import H2M, energy_scale, zeros
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -57,5 +59,8 @@ def test_walker_beyond_shared_memory():
     # ln psi was recomputed after the sweep (recompute_every = 1): equal to a fresh pass
     np.testing.assert_allclose(lp.cpu().numpy(), lpe.cpu().numpy(), rtol=1e-6)
     assert not torch.equal(lp, lp0)
-    # one sweep from the fcc start: bound, attractive energies (about -8.7 K per atom measured)
-    assert np.all((e.cpu().numpy()[:, 4] / n > -15.0) & (e.cpu().numpy()[:, 4] / n < 0.0))
+    # parity: the oracle's local energy of walker 0's final configuration (2 x 10^8 pairs)
+    host = pos.cpu().numpy()
+    blk = host[:3 * pad].reshape(3, pad)[:, :n].astype(np.float64)
+    want = oracle.local_energy(blk, L, qi.B_HE, 5.0, 1, H2M)
+    assert np.all(np.abs(e.cpu().numpy()[0] - want) <= 1e-5 * energy_scale(want)), (e[0], want)

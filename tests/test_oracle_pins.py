@@ -319,6 +319,29 @@ def test_resume_is_bitwise_identical():
     assert np.array_equal(a[3], b2[3])
 
 
+@pytest.mark.parametrize("threads", [1, 3])
+def test_batch_equals_walker_by_walker(threads):
+    """orc_run_batch (the oracle's multi-walker driver: packed coordinates at per-walker offsets,
+    OpenMP over walkers) is orc_run_walker applied to each walker, bit for bit: mixed n (so the
+    offsets are uneven), both proposals, different start sweeps and sums already in accum."""
+    ns = [5, 64, 17, 130]
+    walkers, pos, lp, sw, acc = [], [], [], [], []
+    for w, n in enumerate(ns):
+        L = qi.box_side(n, qi.RHO_HE)
+        walkers.append(oracle.make_walker(n, L, 3.07 - 0.02 * w, step=0.7 + 0.05 * w, proposal=w % 2,
+                                          recompute_every=3, seed=0xBA7C, wid=100 + w))
+        pos.append(qi.jittered_lattice(n, L, 40 + w))
+        lp.append(oracle.log_psi(pos[-1], L, 3.07 - 0.02 * w))
+        sw.append([0, 5, 2, 11][w])
+        acc.append(np.arange(8, dtype=float) * (w + 1))
+    bpos, blp, bsw, bacc, used = oracle.run_batch(walkers, pos, lp, sw, 6, 2, accum=np.array(acc), nthreads=threads)
+    assert used >= 1
+    for w in range(len(ns)):
+        p, l, k, a, _ = oracle.run_walker(walkers[w], pos[w], lp[w], sw[w], 6, 2, accum=acc[w])
+        assert np.array_equal(bpos[w], p) and blp[w] == l and int(bsw[w]) == k
+        assert np.array_equal(bacc[w], a)
+
+
 def test_margins_decide_acceptance():
     n = 16
     L = qi.box_side(n, qi.RHO_HE)

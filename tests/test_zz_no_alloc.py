@@ -76,3 +76,67 @@ def test_static_sweep_rejects_too_many_walkers():
     assert q.lib().qmc_sweep_static(d, len(rows), C.byref(q.options()), C.c_void_p(pos.data_ptr()),
                                     C.c_void_p(lp.data_ptr()), C.c_void_p(sw.data_ptr()), 1, 1, 0,
                                     C.c_void_p(acc.data_ptr()), None, None) == -1
+
+
+@pytest.mark.parametrize("case", ["queue_and_groups", "drift_tile_modes", "hbm_walkers"])
+def test_static_sweep_matches_qmc_sweep_on_other_launch_shapes(case):
+    # qmc_sweep runs these batches through launch shapes the static path never takes: the
+    # persistent walker queue (more walkers than SMs), several walkers per CTA (thousands of small
+    # walkers), the drift arrays of the energy pass in global scratch (n > 2400 at 128 threads per
+    # walker), and walkers too large for shared memory used in place in HBM.  The chains and sums
+    # must be the same, bit for bit (the arithmetic of every move and energy sample is the same).
+    if case == "queue_and_groups":
+        prec, ns, kw = q.QMC_FP64, [64] * 3700, dict(threads_per_walker=32)
+    elif case == "drift_tile_modes":
+        prec, ns, kw = q.QMC_FP32, [2500, 2504, 2404], dict(threads_per_walker=128)
+    else:
+        prec, ns, kw = q.QMC_FP64, [10000, 9700], {}
+        assert min(ns) > q.qmc_capacity(q.QMC_FP64)
+    A = lattice_batch(ns, prec, seed=74)
+    B = lattice_batch(ns, prec, seed=74)
+    opt = q.options(precision=prec, recompute_every=1, **kw)
+    la, sa, aa = _state(A)
+    lb, sb, ab = _state(B)
+    q.qmc_log_psi(A.d, opt, A.pos, la)
+    q.qmc_log_psi(B.d, opt, B.pos, lb)
+    q.qmc_sweep(A.d, opt, A.pos, la, sa, 0xB0B, 1, 1, aa)
+    q.qmc_sweep_static(B.d, opt, B.pos, lb, sb, 0xB0B, 1, 1, ab)
+    assert q.qmc_status(timeout_ms=300000) == 0
+    assert torch.equal(A.pos, B.pos) and torch.equal(sa, sb) and torch.all(sa == 1)
+    assert torch.equal(la, lb) and torch.equal(aa, ab)
+
+
+def test_static_sweep_refuses_stream_capture():
+    # its walker table is staged from host memory that the next call reuses, so a recorded copy
+    # would replay whatever was staged last: the call is refused before anything is enqueued
+    A = lattice_batch([64, 130], q.QMC_FP32, seed=75)
+    lp, sw, acc = _state(A)
+    q.qmc_sweep_static(A.d, q.options(), A.pos, lp, sw, 7, 1, 0, acc)  # first call: outside capture
+    torch.cuda.synchronize()
+    before, marker = A.pos.clone(), zeros(1)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    refused = None
+    with torch.cuda.graph(g, stream=s):
+        try:
+            q.qmc_sweep_static(A.d, q.options(), A.pos, lp, sw, 7, 1, 0, acc)
+        except q.QmcError as e:
+            refused = e
+        marker.add_(1.0)  # the capture itself stays valid
+    assert refused is not None and refused.code == -1 and "capture" in str(refused)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(A.pos, before) and marker.item() == 1.0 and torch.all(sw == 1)
+    assert q.qmc_status(timeout_ms=60000) == 0
+
+
+def test_status_reports_static_path_errors_without_an_err_word():
+    A = lattice_batch([64, 64], q.QMC_FP32, seed=76)
+    A.pos[A.d[1].offset + 3] = float("nan")
+    lp, sw, acc = _state(A)
+    q.qmc_sweep_static(A.d, q.options(), A.pos, lp, sw, 8, 1, 0, acc)  # err = NULL
+    with pytest.raises(q.QmcError, match="bad coordinate"):
+        q.qmc_status(timeout_ms=60000)
+    assert q.qmc_status(timeout_ms=60000) == 0  # read and cleared
+    assert sw.cpu().tolist() == [1, 0]
