@@ -26,6 +26,11 @@
  *               reads; a walker that trips it stops and writes back neither its positions nor
  *               its ln psi and sweep counter (energy samples it took before stay in accum).
  *  Threads:     calls may come from several host threads; the descriptor cache is locked.
+ *  Overlap:     calls with the same walker descriptors share the library's device table of that
+ *               batch, and qmc_sweep calls of a batch with more walkers than SMs also share its
+ *               walker queue: two such qmc_sweep calls must not run at the same time on the GPU
+ *               (issue them on one stream, or order their streams).  Batches with different
+ *               descriptors (for instance other walker ids) are independent.
  *
  * Citations are to sections and equations of the paper.
  */

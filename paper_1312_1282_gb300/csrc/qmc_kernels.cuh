@@ -68,6 +68,23 @@ struct KahanF {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// Sum of one row of pair terms (one atom against all partners) in the row-wise passes.  In FP32
+// the partners go in blocks of ROW_BLOCK 4-atom chunks summed in float, and the block sums are
+// added with compensation: a long row of tiny far-partner terms (u, u', u'' fall off as powers of
+// 1/r) is not lost below the rounding of a large running sum.  In FP64 one block is the row.
+template <typename T> struct RowSum;
+template <> struct RowSum<float> {
+    KahanF k;
+    __device__ __forceinline__ void add(float x) { k.add(x); }
+    __device__ __forceinline__ double value() const { return k.value(); }
+};
+template <> struct RowSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <typename T> constexpr int row_block() { return std::is_same<T, float>::value ? 16 : (1 << 30); }
+
 // the ln psi carried along a chain: double in FP64 mode, compensated floats in FP32 mode
 template <typename T> struct LogPsiAcc {
     double base;
@@ -324,22 +341,27 @@ __device__ double group_log_psi(const Jas<T, MEXP, SYM> &J, const T *sx, const T
     double tot = 0.0;
     for (int i = gtid; i < n; i += TPW) {
         const T xi = sx[i], yi = sy[i], zi = sz[i];
-        T row = (T)0;
-        for (int c = 0; c < nv; ++c) {
-            const V X = reinterpret_cast<const V *>(sx)[c];
-            const V Y = reinterpret_cast<const V *>(sy)[c];
-            const V Z = reinterpret_cast<const V *>(sz)[c];
+        RowSum<T> row;
+        for (int c0 = 0; c0 < nv; c0 += row_block<T>()) {
+            const int c1 = min(nv, c0 + row_block<T>());
+            T blk = (T)0;
+            for (int c = c0; c < c1; ++c) {
+                const V X = reinterpret_cast<const V *>(sx)[c];
+                const V Y = reinterpret_cast<const V *>(sy)[c];
+                const V Z = reinterpret_cast<const V *>(sz)[c];
 #pragma unroll
-            for (int e = 0; e < VN; ++e) {
-                const T ax = mi_abs(xi - Vec<T>::get(X, e), L), ay = mi_abs(yi - Vec<T>::get(Y, e), L),
-                        az = mi_abs(zi - Vec<T>::get(Z, e), L);
-                const T r2 = fma(ax, ax, fma(ay, ay, az * az));
-                const T uu = J.u(r2);
-                const int j = c * VN + e;
-                row += (r2 < hL2 && j != i && j < n) ? uu : (T)0;
+                for (int e = 0; e < VN; ++e) {
+                    const T ax = mi_abs(xi - Vec<T>::get(X, e), L), ay = mi_abs(yi - Vec<T>::get(Y, e), L),
+                            az = mi_abs(zi - Vec<T>::get(Z, e), L);
+                    const T r2 = fma(ax, ax, fma(ay, ay, az * az));
+                    const T uu = J.u(r2);
+                    const int j = c * VN + e;
+                    blk += (r2 < hL2 && j != i && j < n) ? uu : (T)0;
+                }
             }
+            row.add(blk);
         }
-        tot += (double)row;
+        tot += row.value();
     }
     return 0.5 * group_sum<TPW>(tot, redD, phD, bar_id, gtid);
 }
@@ -613,45 +635,55 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
         const bool row = i < n;
         const int ii = row ? i : n - 1;
         const T xi = sx[ii], yi = sy[ii], zi = sz[ii];
-        T v = 0, lap = 0, fx = 0, fy = 0, fz = 0;
-        for (int c = 0; c < nv; ++c) {
-            const V X = reinterpret_cast<const V *>(sx)[c];
-            const V Y = reinterpret_cast<const V *>(sy)[c];
-            const V Z = reinterpret_cast<const V *>(sz)[c];
-            const bool upper = c * VN + VN - 1 > i0;  // some lane of the warp has j > i here
+        RowSum<T> sv, slap, sfx, sfy, sfz;
+        for (int c0 = 0; c0 < nv; c0 += row_block<T>()) {
+            const int c1 = min(nv, c0 + row_block<T>());
+            T v = 0, lap = 0, fx = 0, fy = 0, fz = 0;
+            for (int c = c0; c < c1; ++c) {
+                const V X = reinterpret_cast<const V *>(sx)[c];
+                const V Y = reinterpret_cast<const V *>(sy)[c];
+                const V Z = reinterpret_cast<const V *>(sz)[c];
+                const bool upper = c * VN + VN - 1 > i0;  // some lane of the warp has j > i here
 #pragma unroll
-            for (int e = 0; e < VN; ++e) {
-                const int j = c * VN + e;
-                const T dx = mi_signed(xi - Vec<T>::get(X, e), L, iL);
-                const T dy = mi_signed(yi - Vec<T>::get(Y, e), L, iL);
-                const T dz = mi_signed(zi - Vec<T>::get(Z, e), L, iL);
-                const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                const bool ok = (r2 < hL2) && (j != i) && (j < n);
-                const T q = Fn<T>::rsqrt(r2);
-                const T r = r2 * q;
-                const T f0 = J.fq(q, r);  // f(r) = c r^-m
-                T u1 = -m * f0 * q, u2 = mm1 * f0 * (q * q);
-                if (SYM) {
-                    const T w = L - r, iw = Fn<T>::rcp(w);
-                    const T g0 = J.fq(iw, w);  // f(L - r)
-                    u1 += m * g0 * iw;
-                    u2 += mm1 * g0 * (iw * iw);
-                }
-                const T g = u1 * q;
-                fx += ok ? g * dx : (T)0;
-                fy += ok ? g * dy : (T)0;
-                fz += ok ? g * dz : (T)0;
-                if (upper) {
-                    const bool half = ok && j > i;
-                    lap += half ? fma((T)2 * u1, q, u2) : (T)0;
-                    v += half ? aziz(r, q) : (T)0;
+                for (int e = 0; e < VN; ++e) {
+                    const int j = c * VN + e;
+                    const T dx = mi_signed(xi - Vec<T>::get(X, e), L, iL);
+                    const T dy = mi_signed(yi - Vec<T>::get(Y, e), L, iL);
+                    const T dz = mi_signed(zi - Vec<T>::get(Z, e), L, iL);
+                    const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    const bool ok = (r2 < hL2) && (j != i) && (j < n);
+                    const T q = Fn<T>::rsqrt(r2);
+                    const T r = r2 * q;
+                    const T f0 = J.fq(q, r);  // f(r) = c r^-m
+                    T u1 = -m * f0 * q, u2 = mm1 * f0 * (q * q);
+                    if (SYM) {
+                        const T w = L - r, iw = Fn<T>::rcp(w);
+                        const T g0 = J.fq(iw, w);  // f(L - r)
+                        u1 += m * g0 * iw;
+                        u2 += mm1 * g0 * (iw * iw);
+                    }
+                    const T g = u1 * q;
+                    fx += ok ? g * dx : (T)0;
+                    fy += ok ? g * dy : (T)0;
+                    fz += ok ? g * dz : (T)0;
+                    if (upper) {
+                        const bool half = ok && j > i;
+                        lap += half ? fma((T)2 * u1, q, u2) : (T)0;
+                        v += half ? aziz(r, q) : (T)0;
+                    }
                 }
             }
+            sv.add(v);
+            slap.add(lap);
+            sfx.add(fx);
+            sfy.add(fy);
+            sfz.add(fz);
         }
         if (row) {
-            sV += (double)v;
-            sLap += 2.0 * (double)lap;  // each pair's Laplacian term belongs to both atoms
-            sF2 += (double)fx * fx + (double)fy * fy + (double)fz * fz;
+            const double fx = sfx.value(), fy = sfy.value(), fz = sfz.value();
+            sV += sv.value();
+            sLap += 2.0 * slap.value();  // each pair's Laplacian term belongs to both atoms
+            sF2 += fx * fx + fy * fy + fz * fz;
         }
     }
     sV = group_sum<TPW>(sV, redD, phD, bar_id, gtid);
@@ -1486,58 +1518,74 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
     double sLp = 0, sLpm = 0, sV = 0, sLap = 0, sLapm = 0, sF2 = 0, sFFm = 0;
     for (int i = gtid; i < n; i += TPW) {
         const T xi = sx[i], yi = sy[i], zi = sz[i];
-        T lp = 0, lpm = 0, v = 0, lap = 0, lapm = 0, fx = 0, fy = 0, fz = 0, gx_ = 0, gy_ = 0, gz_ = 0;
-        for (int cc = 0; cc < nv; ++cc) {
-            const V X = reinterpret_cast<const V *>(sx)[cc];
-            const V Y = reinterpret_cast<const V *>(sy)[cc];
-            const V Z = reinterpret_cast<const V *>(sz)[cc];
+        RowSum<T> a_lp, a_lpm, a_v, a_lap, a_lapm, a_fx, a_fy, a_fz, a_gx, a_gy, a_gz;
+        for (int c0 = 0; c0 < nv; c0 += row_block<T>()) {
+            const int cend = min(nv, c0 + row_block<T>());
+            T lp = 0, lpm = 0, v = 0, lap = 0, lapm = 0, fx = 0, fy = 0, fz = 0, gx_ = 0, gy_ = 0, gz_ = 0;
+            for (int cc = c0; cc < cend; ++cc) {
+                const V X = reinterpret_cast<const V *>(sx)[cc];
+                const V Y = reinterpret_cast<const V *>(sy)[cc];
+                const V Z = reinterpret_cast<const V *>(sz)[cc];
 #pragma unroll
-            for (int e = 0; e < VN; ++e) {
-                const T dx = mi_signed(xi - Vec<T>::get(X, e), L, iL);
-                const T dy = mi_signed(yi - Vec<T>::get(Y, e), L, iL);
-                const T dz = mi_signed(zi - Vec<T>::get(Z, e), L, iL);
-                const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                const bool ok = (r2 < hL2) && (cc * VN + e != i) && (cc * VN + e < n);
-                const T q = Fn<T>::rsqrt(r2);
-                const T r = r2 * q;
-                const T lbr = lnb + Fn<T>::log(q);  // ln(b/r)
-                const T f = c * Fn<T>::powneg(r, m);
-                const T f1 = -m * f * q, f2 = m * (m + (T)1) * f * (q * q);
-                T uu = f, u1 = f1, u2 = f2, um = f * lbr, u1m = f1 * (c1 + lbr), u2m = f2 * (c2 + lbr);
-                if (SYM) {
-                    const T w = L - r, iw = Fn<T>::rcp(w);
-                    const T lbw = lnb + Fn<T>::log(iw);
-                    const T g = c * Fn<T>::powneg(w, m);
-                    const T g1 = -m * g * iw, g2 = m * (m + (T)1) * g * (iw * iw);
-                    uu += g - K;
-                    u1 -= g1;
-                    u2 += g2;
-                    um += g * lbw - Km;
-                    u1m -= g1 * (c1 + lbw);
-                    u2m += g2 * (c2 + lbw);
+                for (int e = 0; e < VN; ++e) {
+                    const T dx = mi_signed(xi - Vec<T>::get(X, e), L, iL);
+                    const T dy = mi_signed(yi - Vec<T>::get(Y, e), L, iL);
+                    const T dz = mi_signed(zi - Vec<T>::get(Z, e), L, iL);
+                    const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    const bool ok = (r2 < hL2) && (cc * VN + e != i) && (cc * VN + e < n);
+                    const T q = Fn<T>::rsqrt(r2);
+                    const T r = r2 * q;
+                    const T lbr = lnb + Fn<T>::log(q);  // ln(b/r)
+                    const T f = c * Fn<T>::powneg(r, m);
+                    const T f1 = -m * f * q, f2 = m * (m + (T)1) * f * (q * q);
+                    T uu = f, u1 = f1, u2 = f2, um = f * lbr, u1m = f1 * (c1 + lbr), u2m = f2 * (c2 + lbr);
+                    if (SYM) {
+                        const T w = L - r, iw = Fn<T>::rcp(w);
+                        const T lbw = lnb + Fn<T>::log(iw);
+                        const T g = c * Fn<T>::powneg(w, m);
+                        const T g1 = -m * g * iw, g2 = m * (m + (T)1) * g * (iw * iw);
+                        uu += g - K;
+                        u1 -= g1;
+                        u2 += g2;
+                        um += g * lbw - Km;
+                        u1m -= g1 * (c1 + lbw);
+                        u2m += g2 * (c2 + lbw);
+                    }
+                    const T vv = aziz(r, q);
+                    lp += ok ? uu : (T)0;
+                    lpm += ok ? um : (T)0;
+                    v += ok ? vv : (T)0;
+                    lap += ok ? fma((T)2 * u1, q, u2) : (T)0;
+                    lapm += ok ? fma((T)2 * u1m, q, u2m) : (T)0;
+                    const T g0 = u1 * q, gm = u1m * q;
+                    fx += ok ? g0 * dx : (T)0;
+                    fy += ok ? g0 * dy : (T)0;
+                    fz += ok ? g0 * dz : (T)0;
+                    gx_ += ok ? gm * dx : (T)0;
+                    gy_ += ok ? gm * dy : (T)0;
+                    gz_ += ok ? gm * dz : (T)0;
                 }
-                const T vv = aziz(r, q);
-                lp += ok ? uu : (T)0;
-                lpm += ok ? um : (T)0;
-                v += ok ? vv : (T)0;
-                lap += ok ? fma((T)2 * u1, q, u2) : (T)0;
-                lapm += ok ? fma((T)2 * u1m, q, u2m) : (T)0;
-                const T g0 = u1 * q, gm = u1m * q;
-                fx += ok ? g0 * dx : (T)0;
-                fy += ok ? g0 * dy : (T)0;
-                fz += ok ? g0 * dz : (T)0;
-                gx_ += ok ? gm * dx : (T)0;
-                gy_ += ok ? gm * dy : (T)0;
-                gz_ += ok ? gm * dz : (T)0;
             }
+            a_lp.add(lp);
+            a_lpm.add(lpm);
+            a_v.add(v);
+            a_lap.add(lap);
+            a_lapm.add(lapm);
+            a_fx.add(fx);
+            a_fy.add(fy);
+            a_fz.add(fz);
+            a_gx.add(gx_);
+            a_gy.add(gy_);
+            a_gz.add(gz_);
         }
-        sLp += (double)lp;
-        sLpm += (double)lpm;
-        sV += (double)v;
-        sLap += (double)lap;
-        sLapm += (double)lapm;
-        sF2 += (double)fx * fx + (double)fy * fy + (double)fz * fz;
-        sFFm += (double)fx * gx_ + (double)fy * gy_ + (double)fz * gz_;
+        const double fx = a_fx.value(), fy = a_fy.value(), fz = a_fz.value();
+        sLp += a_lp.value();
+        sLpm += a_lpm.value();
+        sV += a_v.value();
+        sLap += a_lap.value();
+        sLapm += a_lapm.value();
+        sF2 += fx * fx + fy * fy + fz * fz;
+        sFFm += fx * a_gx.value() + fy * a_gy.value() + fz * a_gz.value();
     }
     sLp = group_sum<TPW>(sLp, redD, phD, 1, gtid);
     sLpm = group_sum<TPW>(sLpm, redD, phD, 1, gtid);

@@ -33,10 +33,13 @@ def test_graph_replays_equal_uncaptured_calls(prec, mixed):
     q.qmc_log_psi(A.d, opt, A.pos, la)
     q.qmc_log_psi(B.d, opt, B.pos, lb)
     seed, nsw, every, k = 0x6A7, 2, 1, 3
+    # A and B have the same descriptors, so they share the library's walker table and queue:
+    # their calls must not overlap on the GPU
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):  # the uncaptured first call of the batch on both sides
+    with torch.cuda.stream(s):  # the uncaptured first call of the batch, on the capture stream
         q.qmc_sweep(A.d, opt, A.pos, la, sa, seed, nsw, every, aa)
+    torch.cuda.synchronize()
     q.qmc_sweep(B.d, opt, B.pos, lb, sb, seed, nsw, every, ab)
     torch.cuda.synchronize()
     launches = q.qmc_launch_count()
@@ -47,6 +50,7 @@ def test_graph_replays_equal_uncaptured_calls(prec, mixed):
     assert captured == 2  # queue initialisation and the persistent (or mixed) sweep
     for _ in range(k):
         g.replay()
+    torch.cuda.synchronize()
     for _ in range(k):
         q.qmc_sweep(B.d, opt, B.pos, lb, sb, seed, nsw, every, ab)
     torch.cuda.synchronize()
