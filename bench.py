@@ -235,7 +235,7 @@ def run_native(args):
     torch.cuda.synchronize()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    # measured arithmetic rates of this GPU (per clock per SM), outside the timed region
+    # measured arithmetic rates of this GPU (per second per SM), outside the timed region
     probe = q.qmc_probe_rates(4, 256, 2000)
 
     def one_step():
@@ -404,11 +404,13 @@ def run_native(args):
             "energy_pass": {"ms_per_sample": energy_ms, "pairs_per_s": energy_pairs * world / (energy_ms * 1e-3),
                             "achieved_tops": energy_ops, "frac": energy_ops / peak_tops,
                             "how": "step time minus the median of 3 steps without the energy sample"},
-            "probe": {"per_clock_per_sm": probe, "how": "qmc_probe_rates(4 CTAs/SM, 256 threads, 2000 iters)",
+            "probe": {"per_clock_per_sm": {k: v / (clk * 1e6) for k, v in probe.items()},
+                      "how": "qmc_probe_rates(4 CTAs/SM, 256 threads, 2000 iters), CUDA events; per clock at the "
+                             "run's maximum SM clock",
                       "pair_evals_per_clock_per_sm_achieved": value / world / (nsm * clk * 1e6),
-                      "pair_evals_ceiling_of_probe": probe["pair_evals"],
-                      "ffma2_peak_tops": probe["ffma2"] * nsm * clk * 1e6 / 1e12,
-                      "frac_of_probed_ffma2": achieved / (probe["ffma2"] * nsm * clk * 1e6 / 1e12)},
+                      "pair_evals_per_clock_per_sm_of_probe": probe["pair_evals"] / (clk * 1e6),
+                      "ffma_measured_tops": probe["ffma"] * nsm / 1e12,
+                      "frac_of_measured_ffma": achieved / (probe["ffma"] * nsm / 1e12)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
                          "frac": achieved / peak_tops, "traffic": traffic,
                          "note": f"FP32-pipe lane ops ({C_PAIR:g}/pair eval, {C_ENERGY:g}/energy pair) vs "
@@ -901,13 +903,18 @@ def run_pipes(args):
     import paper_1312_1282_gb300 as q
     torch.cuda.set_device(0)
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    clocks = ClockSampler(_bus_id(torch, 0))
+    clocks.start()
+    time.sleep(0.3)
     rows = []
     for bps, thr in ((2, 128), (4, 128), (4, 256), (2, 512), (1, 1024), (8, 128), (3, 512)):
-        q.qmc_probe_rates(bps, thr, 200)  # warm
-        rows.append({"ctas_per_sm": bps, "threads": thr, "warps_per_sm": bps * thr // 32,
-                     **q.qmc_probe_rates(bps, thr, 4000)})
-    print(json.dumps({"config": "arithmetic rates per clock per SM (qmc_probe_rates)", "sms": nsm, "rows": rows}),
-          flush=True)
+        rows.append({"ctas_per_sm": bps, "threads": thr, "per_second_per_sm": q.qmc_probe_rates(bps, thr, 4000)})
+    clock = clocks.stop()
+    mhz = clock.get("sm_max_mhz") or _peaks().get("sm_max_mhz") or 2070.0
+    for r in rows:
+        r["per_clock_per_sm"] = {k: v / (mhz * 1e6) for k, v in r["per_second_per_sm"].items()}
+    print(json.dumps({"config": "arithmetic rates of this GPU (qmc_probe_rates, CUDA events)", "sms": nsm,
+                      "clock_mhz_for_per_clock": mhz, "clocks": clock, "rows": rows}), flush=True)
     return 0
 
 

@@ -13,8 +13,9 @@
 extern "C" {
 #endif
 
-/* Indices of qmc_probe_rates' results: lane operations per clock per SM, except the last, which
- * is pair evaluations per clock per SM. */
+/* Indices of qmc_probe_rates' results: lane operations per second per SM, except the last,
+ * which is pair evaluations per second per SM.  Divided by the SM clock of the run they give the
+ * rates per clock. */
 #define QMC_PROBE_FFMA 0      /* FP32 fused multiply-add, scalar (fma.rn.f32) */
 #define QMC_PROBE_FFMA2 1     /* FP32 fused multiply-add, packed pairs (fma.rn.f32x2), 2 per instruction */
 #define QMC_PROBE_FMNMX 2     /* FP32 minimum (min.f32) */
@@ -27,10 +28,12 @@ extern "C" {
 
 /*
  * qmc_probe_rates -- run each probe kernel on blocks_per_sm x (SM count) CTAs of `threads`
- * threads (a multiple of 32, 32..1024) for `iters` loop iterations (1..1e6) on `stream`; every
- * CTA reads the SM clock (clock64) around its loop, and the rate is the operations of the CTAs of
- * one SM over their mean clock count.  Eight (pair probe: four) independent dependency chains per
- * thread; the operations are inline PTX, so none is folded away.
+ * threads (a multiple of 32, 32..1024; the pair probe at most 512) for `iters` loop iterations
+ * (1..1e6) on `stream`, after a short warm-up launch, and time it with CUDA events; the rate is
+ * the operations of all CTAs over the elapsed time and the SM count (the CTAs are spread evenly,
+ * all resident at once; fewer per SM if the kernel's occupancy is lower).  Eight (pair probe:
+ * four) independent dependency chains per thread; the operations are inline PTX on values that
+ * change every iteration, so none is folded away or hoisted out of the loop.
  *   out    host array of QMC_PROBE_COUNT doubles, written on success.
  * Allocates and frees a small device buffer, synchronises the stream.  Returns QMC_OK, QMC_ERR_ARG
  * for out-of-range arguments or QMC_ERR_CUDA.  Not for use during stream capture.

@@ -230,7 +230,7 @@ PROBE_FIELDS = ("ffma", "ffma2", "fmnmx", "rsqrt", "dfma", "pair_evals")
 
 
 def qmc_probe_rates(blocks_per_sm=4, threads=256, iters=2000, stream=None) -> dict:
-    """Measured rates per clock per SM on the current GPU (include/qmc_probe.h): lane operations
+    """Measured rates per second per SM on the current GPU (include/qmc_probe.h): lane operations
     of FP32 FMA (scalar, packed), FP32 min, SFU rsqrt, FP64 FMA, and pair evaluations of the
     sweep's partner arithmetic alone."""
     out = (C.c_double * len(PROBE_FIELDS))()

@@ -77,6 +77,9 @@ struct Plan {
     uint2 *q_slots = nullptr;  // walker FIFO of the persistent sweep
     int *q_prog = nullptr;
     unsigned *q_ctr = nullptr;  // head, tail, next dominant walker (mixed sweep)
+    double *part_out = nullptr;  // shares of split passes: W x parts x 8 doubles (grown on demand)
+    unsigned *part_ctr = nullptr;  // [W] finished parts per walker, zero between launches
+    size_t part_cap = 0;
     int maxn = 0, maxpad = 0, maxsites = 0;
     bool m5 = true;
 };
@@ -304,6 +307,8 @@ void free_plan(Plan *p)
     if (p->q_slots) cudaFree(p->q_slots);
     if (p->q_prog) cudaFree(p->q_prog);
     if (p->q_ctr) cudaFree(p->q_ctr);
+    if (p->part_out) cudaFree(p->part_out);
+    if (p->part_ctr) cudaFree(p->part_ctr);
     delete p;
 }
 
@@ -792,6 +797,42 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     return QMC_OK;
 }
 
+// CTAs per walker of a row-wise pass: with fewer walkers than SMs, a walker's rows are split over
+// about SMs / W CTAs (at least one block of tpw rows each), so that few large walkers use the GPU.
+int choose_parts(const Plan &P, int W, int nsm, int tpw)
+{
+    if (W >= nsm) return 1;
+    const int by_rows = (P.maxn + tpw - 1) / tpw;
+    return std::max(1, std::min({nsm / W, by_rows, 64}));
+}
+
+// the plan's scratch of split passes, at least W x parts x 8 doubles, and its zeroed counters
+// (allocated on first use: not under stream capture)
+int pass_scratch(Plan &P, int parts, cudaStream_t st, double **out, unsigned **ctr)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    const size_t need = (size_t)P.W * parts * 8;
+    if (P.part_cap < need) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            return fail(QMC_ERR_ARG, "a split pass of this batch needs its scratch allocated before stream capture; "
+                                     "call it once outside capture");
+        if (P.part_out) cudaFree(P.part_out);
+        P.part_out = nullptr;
+        P.part_cap = 0;
+        cudaError_t e = cudaMalloc(&P.part_out, need * sizeof(double));
+        if (e == cudaSuccess && !P.part_ctr) {
+            e = cudaMalloc(&P.part_ctr, sizeof(unsigned) * (size_t)P.W);
+            if (e == cudaSuccess) e = cudaMemsetAsync(P.part_ctr, 0, sizeof(unsigned) * (size_t)P.W, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "split-pass scratch");
+        P.part_cap = need;
+    }
+    *out = P.part_out;
+    *ctr = P.part_ctr;
+    return QMC_OK;
+}
+
 int pass_impl(const qmc_walker_desc *d, int W, const qmc_options *o, const void *pos, double *out, int kind,
               const int32_t *s, const double *delta, int M, cudaStream_t st)
 {
@@ -815,8 +856,14 @@ int pass_impl(const qmc_walker_desc *d, int W, const qmc_options *o, const void 
     a.delta = delta;
     a.M = M;
     a.err = p.ds->err;
+    // row-wise passes of few walkers are split over several CTAs per walker (the tiled energy
+    // pass and the trial ratios are not)
+    a.parts = (kind == 2 || (kind == 0 && sh.tile)) ? 1 : choose_parts(P, W, p.ds->nsm, tpw);
+    a.part_out = nullptr;
+    a.part_ctr = nullptr;
+    if (a.parts > 1 && (rc = pass_scratch(*p.plan, a.parts, st, &a.part_out, &a.part_ctr))) return rc;
     const size_t smem = sh.smem;
-    cudaError_t e = launch_pass(o->precision, variant_of(P, o), kind, W, smem, st, a);
+    cudaError_t e = launch_pass(o->precision, variant_of(P, o), kind, W * a.parts, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "pass launch");
     g_launches.fetch_add(1);
     return QMC_OK;
@@ -899,9 +946,13 @@ int qmc_pair_hist(const qmc_walker_desc *d, int W, const qmc_options *opt, const
     a.delta = nullptr;
     a.M = 0;
     a.err = p.ds->err;
+    a.parts = choose_parts(P, W, p.ds->nsm, PASS_TPW);  // counts of the parts add with atomics
+    a.part_out = nullptr;
+    a.part_ctr = nullptr;
     const size_t smem = sh.smem + sizeof(unsigned) * (size_t)nbins;
     if (smem > MAX_SMEM) return fail(QMC_ERR_CAPACITY, "histogram does not fit shared memory next to the walker");
-    cudaError_t e = launch_hist(opt->precision, W, smem, st, a, nbins, rmax, reinterpret_cast<unsigned long long *>(hist));
+    cudaError_t e = launch_hist(opt->precision, W * a.parts, smem, st, a, nbins, rmax,
+                                reinterpret_cast<unsigned long long *>(hist));
     if (e != cudaSuccess) return cuda_fail(e, "histogram launch");
     g_launches.fetch_add(1);
     return QMC_OK;
@@ -1042,11 +1093,11 @@ int qmc_probe_rates(int blocks_per_sm, int threads, int iters, double *out, void
     DeviceState *ds;
     if ((rc = device_state(dev, ds))) return rc;
     const int nsm = ds->nsm;
-    long long *cycles = nullptr;
     float *sink = nullptr;
-    cudaError_t e = cudaMalloc(&cycles, sizeof(long long) * (size_t)blocks_per_sm * nsm);
-    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float) * (size_t)blocks_per_sm * nsm * threads);
-    std::vector<long long> host((size_t)blocks_per_sm * nsm);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(float) * (size_t)blocks_per_sm * nsm * threads);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double res[QMC_PROBE_COUNT] = {};
     for (int kind = 0; e == cudaSuccess && kind < QMC_PROBE_COUNT; ++kind) {
         // the pair probe keeps the sweep's register budget: at most 512 threads per CTA
@@ -1059,18 +1110,20 @@ int qmc_probe_rates(int blocks_per_sm, int threads, int iters, double *out, void
             e = cudaErrorInvalidConfiguration;
             break;
         }
-        const int grid = resident * nsm;  // every CTA resident at once
-        e = launch_probe(kind, grid, thr, iters, cycles, sink, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), cycles, sizeof(long long) * grid, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        const int grid = resident * nsm;  // every CTA resident at once, the same number on every SM
+        e = launch_probe(kind, grid, thr, std::max(1, iters / 16), sink, st);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = launch_probe(kind, grid, thr, iters, sink, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e != cudaSuccess) break;
-        g_launches.fetch_add(1);
-        double mean = 0;
-        for (int b = 0; b < grid; ++b) mean += (double)host[b];
-        mean /= grid;
-        res[kind] = resident * (double)thr * iters * probe_ops_per_thread_iter(kind) / mean;
+        g_launches.fetch_add(2);
+        res[kind] = (double)grid * thr * iters * probe_ops_per_thread_iter(kind) / (ms * 1e-3) / nsm;
     }
-    if (cycles) cudaFree(cycles);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     if (sink) cudaFree(sink);
     if (e != cudaSuccess) return cuda_fail(e, "probe");
     for (int k = 0; k < QMC_PROBE_COUNT; ++k) out[k] = res[k];

@@ -186,10 +186,10 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
 #pragma unroll
             for (int w = 1; w < NW; ++w) s += red[gtid * NW + w];
             float *slot = &part[(ph * K + gtid) * 8 + rank];
-            for (int r = 0; r < C; ++r) {
-                st_cluster(map_rank(slot, (unsigned)r), s);
-                mb_arrive_remote(map_rank(&mb[ph], (unsigned)r));
-            }
+            // all stores first, then the arrives: each release arrive orders every earlier store
+            // of this thread, so the C stores travel together instead of one round trip each
+            for (int r = 0; r < C; ++r) st_cluster(map_rank(slot, (unsigned)r), s);
+            for (int r = 0; r < C; ++r) mb_arrive_remote(map_rank(&mb[ph], (unsigned)r));
         }
         if (!tmo && !mb_wait_cluster(&mb[ph], par, a.wait_ns, a.err)) tmo = true;
 #pragma unroll

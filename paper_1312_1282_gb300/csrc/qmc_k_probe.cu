@@ -1,6 +1,7 @@
 // Calibration kernels of qmc_probe_rates (include/qmc_probe.h): loops of one arithmetic operation
-// (inline PTX, so the compiler can neither fold nor drop them) and a loop of the sweep's FP32
-// partner arithmetic alone, each CTA reading the SM clock around its loop.
+// (inline PTX on values that change every iteration, so that nothing can be folded, hoisted or
+// dropped) and a loop of the sweep's FP32 partner arithmetic alone.  The host times each launch
+// with CUDA events.
 #include "qmc_launch.h"
 
 namespace qmc {
@@ -29,7 +30,7 @@ __device__ __forceinline__ unsigned long long pack2(float x, float y)
 }
 
 // KIND: 0 FFMA, 1 FFMA2, 2 FMNMX, 3 RSQRT, 4 DFMA (QMC_PROBE_* of qmc_probe.h)
-template <int KIND> __global__ void __launch_bounds__(1024) op_probe_kernel(int iters, long long *cycles, float *sink)
+template <int KIND> __global__ void __launch_bounds__(1024) op_probe_kernel(int iters, float *sink)
 {
     const float s = 1.0f + 1e-3f * (float)(threadIdx.x & 7);
     float f[PROBE_CHAINS];
@@ -43,34 +44,32 @@ template <int KIND> __global__ void __launch_bounds__(1024) op_probe_kernel(int 
     }
     const float b = 0.999f, c = 1e-3f;
     const unsigned long long b2 = pack2(b, b), c2 = pack2(c, c);
-    __syncthreads();
-    const long long t0 = clock64();
     for (int it = 0; it < iters; ++it) {
+        // the min probe's other operand changes every iteration (min with a constant would be
+        // idempotent and could be folded)
+        const float v = __int_as_float(0x3f800000 + (it & 0xfff));
 #pragma unroll
         for (int u = 0; u < PROBE_UNROLL; ++u)
 #pragma unroll
             for (int k = 0; k < PROBE_CHAINS; ++k) {
                 if (KIND == 0) op_ffma(f[k], b, c);
                 if (KIND == 1) op_ffma2(p[k], b2, c2);
-                if (KIND == 2) op_fmin(f[k], s);
+                if (KIND == 2) op_fmin(f[k], (u & 1) ? v : s);
                 if (KIND == 3) op_rsqrt(f[k]);
                 if (KIND == 4) op_dfma(g[k], 0.999, 1e-3);
             }
     }
-    __syncthreads();
-    const long long t1 = clock64();
     float r = 0.f;
 #pragma unroll
     for (int k = 0; k < PROBE_CHAINS; ++k) r += f[k] + __uint_as_float((unsigned)p[k]) + (float)g[k];
     sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
 // The partner arithmetic of the FP32 sweep (Packed5::acc5, exponent 5, symmetrised u) for two
 // moves at once, old and new position, over PROBE_PAIR_CHUNKS x 4 partners in shared memory:
 // 16 pair evaluations per chunk, four chunks per thread per iteration, no reduction or barrier.
 constexpr int PROBE_PAIR_CHUNKS_PER_THREAD = 4;
-__global__ void __launch_bounds__(512) pair_probe_kernel(int iters, long long *cycles, float *sink)
+__global__ void __launch_bounds__(512) pair_probe_kernel(int iters, float *sink)
 {
     extern __shared__ __align__(16) float4 part[];  // x | y | z chunks
     const int nv = PROBE_PAIR_CHUNKS_PER_THREAD * blockDim.x;
@@ -93,13 +92,16 @@ __global__ void __launch_bounds__(512) pair_probe_kernel(int iters, long long *c
     const float a0 = 0.37f * L + 1e-3f * (threadIdx.x & 31), a1 = 0.61f * L;
     float2 acco0 = make_float2(0.f, 0.f), accn0 = acco0, acco1 = acco0, accn1 = acco0;
     __syncthreads();
-    const long long t0 = clock64();
     for (int it = 0; it < iters; ++it) {
-        const float e = 1e-6f * (float)(it & 15);  // the moved positions change with the iteration
+        // the moved positions (all three coordinates) and the partners a thread reads change with
+        // the iteration, so no part of the loop body is invariant
+        const float e = 1e-3f * (float)(it & 15);
         const float2 nax0 = make_float2(-(a0 + e), -(a0 + e)), nbx0 = make_float2(-(a0 + 0.5f), -(a0 + 0.5f));
         const float2 nax1 = make_float2(-(a1 - e), -(a1 - e)), nbx1 = make_float2(-(a1 - 0.4f), -(a1 - 0.4f));
-        const float2 ny = make_float2(-0.5f * L, -0.5f * L), nz = make_float2(-0.25f * L, -0.25f * L);
-        for (int c = threadIdx.x; c < nv; c += blockDim.x) {
+        const float2 ny = make_float2(-(0.5f * L + e), -(0.5f * L + e)), nz = make_float2(-(0.25f * L - e), -(0.25f * L - e));
+        const int rot = it % nv;
+        for (int c0 = threadIdx.x; c0 < nv; c0 += blockDim.x) {
+            const int c = c0 + rot < nv ? c0 + rot : c0 + rot - nv;
             const float4 X = part[c], Y = part[nv + c], Z = part[2 * nv + c];
             const float2 xa = make_float2(X.x, X.y), xb = make_float2(X.z, X.w);
             const float2 ya = make_float2(Y.x, Y.y), yb = make_float2(Y.z, Y.w);
@@ -114,11 +116,8 @@ __global__ void __launch_bounds__(512) pair_probe_kernel(int iters, long long *c
             P.acc5(__fadd2_rn(xb, nbx1), __fadd2_rn(yb, ny), __fadd2_rn(zb, nz), accn1);
         }
     }
-    __syncthreads();
-    const long long t1 = clock64();
     sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] =
         acco0.x + acco0.y + accn0.x + accn0.y + acco1.x + acco1.y + accn1.x + accn1.y;
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
 size_t probe_smem(int kind, int threads);
@@ -154,19 +153,19 @@ size_t probe_smem(int kind, int threads)
     return kind == QMC_PROBE_PAIR ? (size_t)3 * PROBE_PAIR_CHUNKS_PER_THREAD * threads * sizeof(float4) : 0;
 }
 
-cudaError_t launch_probe(int kind, int grid, int threads, int iters, long long *cycles, float *sink, cudaStream_t st)
+cudaError_t launch_probe(int kind, int grid, int threads, int iters, float *sink, cudaStream_t st)
 {
     const size_t smem = probe_smem(kind, threads);
     switch (kind) {
-    case QMC_PROBE_FFMA: op_probe_kernel<0><<<grid, threads, 0, st>>>(iters, cycles, sink); break;
-    case QMC_PROBE_FFMA2: op_probe_kernel<1><<<grid, threads, 0, st>>>(iters, cycles, sink); break;
-    case QMC_PROBE_FMNMX: op_probe_kernel<2><<<grid, threads, 0, st>>>(iters, cycles, sink); break;
-    case QMC_PROBE_RSQRT: op_probe_kernel<3><<<grid, threads, 0, st>>>(iters, cycles, sink); break;
-    case QMC_PROBE_DFMA: op_probe_kernel<4><<<grid, threads, 0, st>>>(iters, cycles, sink); break;
+    case QMC_PROBE_FFMA: op_probe_kernel<0><<<grid, threads, 0, st>>>(iters, sink); break;
+    case QMC_PROBE_FFMA2: op_probe_kernel<1><<<grid, threads, 0, st>>>(iters, sink); break;
+    case QMC_PROBE_FMNMX: op_probe_kernel<2><<<grid, threads, 0, st>>>(iters, sink); break;
+    case QMC_PROBE_RSQRT: op_probe_kernel<3><<<grid, threads, 0, st>>>(iters, sink); break;
+    case QMC_PROBE_DFMA: op_probe_kernel<4><<<grid, threads, 0, st>>>(iters, sink); break;
     case QMC_PROBE_PAIR: {
         cudaError_t e = cudaFuncSetAttribute(pair_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
         if (e != cudaSuccess) return e;
-        pair_probe_kernel<<<grid, threads, smem, st>>>(iters, cycles, sink);
+        pair_probe_kernel<<<grid, threads, smem, st>>>(iters, sink);
         break;
     }
     default: return cudaErrorInvalidValue;

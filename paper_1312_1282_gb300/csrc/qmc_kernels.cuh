@@ -9,10 +9,10 @@
 // Work split: a CTA holds G walkers, each served by a group of TPW threads (TPW a multiple of
 // 32).  For one move every thread of the group evaluates the old and new pair terms of its
 // partner chunks j = 4c..4c+3, c = gtid, gtid + TPW, ...; the group sums them (warp butterfly,
-// then one named barrier), and every thread takes the same accept/reject decision.  The owner of
-// the moved atom's chunk writes its new coordinates; all other threads keep a private copy of
-// the last batch's accepted moves, so a batch of moves (two in FP32 for groups of 64 threads or
-// more, one otherwise) needs exactly one group barrier (none for TPW = 32).
+// then one named barrier), and every thread takes the same accept/reject decision.  Every thread
+// writes the accepted coordinates itself (the same values to the same addresses), so every later
+// read of them is of its own write, and a batch of moves (two in FP32 for groups of 64 threads
+// or more, one otherwise) needs exactly one group barrier (none for TPW = 32).
 #pragma once
 
 #include <cuda/atomic>
@@ -333,13 +333,13 @@ struct Packed5 {
 // ln psi = sum_{i<j} u(r_ij) (Eq. Jastrow): full rows, halved.  FP32 row sums, double totals.
 template <typename T, int MEXP, bool SYM, int TPW>
 __device__ double group_log_psi(const Jas<T, MEXP, SYM> &J, const T *sx, const T *sy, const T *sz, int n, int nv,
-                                double *redD, int &phD, int bar_id, int gtid)
+                                double *redD, int &phD, int bar_id, int gtid, int part = 0, int parts = 1)
 {
     using V = typename Vec<T>::type;
     constexpr int VN = Vec<T>::N;
     const T L = J.L, hL2 = J.hL2;
     double tot = 0.0;
-    for (int i = gtid; i < n; i += TPW) {
+    for (int i = part * TPW + gtid; i < n; i += parts * TPW) {  // this CTA's share of the rows
         const T xi = sx[i], yi = sy[i], zi = sz[i];
         RowSum<T> row;
         for (int c0 = 0; c0 < nv; c0 += row_block<T>()) {
@@ -620,17 +620,20 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
 // F_i = sum_j u'(r) (r_i - r_j)/r needs every ordered pair; V and the Laplacian term
 // u'' + 2u'/r are symmetric, so they are taken once per pair (j > i) and the warp skips them
 // for chunks that lie wholly at or below its block's first row.
-// out = {V, T_L, T_PB, T_F, E_L}, valid in every thread of the group.
+// out = {V, T_L, T_PB, T_F, E_L}, valid in every thread of the group.  With parts > 1 the group
+// takes rows part*TPW .. of every parts*TPW and out holds that share (every output is linear in
+// the row sums, so the shares of all parts add up to the walker's values).
 template <typename T, int MEXP, bool SYM, int TPW>
 __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *sy, const T *sz, int n, int nv,
-                             double h2m, double *redD, int &phD, int bar_id, int gtid, double out[5])
+                             double h2m, double *redD, int &phD, int bar_id, int gtid, double out[5], int part = 0,
+                             int parts = 1)
 {
     using V = typename Vec<T>::type;
     constexpr int VN = Vec<T>::N;
     const T L = J.L, iL = (T)1 / J.L, hL2 = J.hL2, m = J.m, mm1 = J.m * (J.m + (T)1);
     const int lane = gtid & 31;
     double sV = 0.0, sLap = 0.0, sF2 = 0.0;
-    for (int i0 = gtid - lane; i0 < n; i0 += TPW) {  // warp-uniform
+    for (int i0 = part * TPW + gtid - lane; i0 < n; i0 += parts * TPW) {  // warp-uniform; this CTA's rows
         const int i = i0 + lane;
         const bool row = i < n;
         const int ii = row ? i : n - 1;
@@ -709,35 +712,6 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
 // Delta_i = S_i + sum_{k < i, accepted} D_ik is Eq. (JastrowUpdate) for the true configuration.
 // A batch that draws the same atom twice is done one move at a time.
 // ----------------------------------------------------------------------------------------------
-// Accepted moves of the previous batch (a private copy per thread), appended in batch order.
-// With two or more moves per batch the entries are addressed by the running count, so the
-// compiler keeps them in local memory (L1): measured faster at N = 1952, 128 threads per walker
-// (20.9 against 21.7 ms per step) than entries held in registers across the partner loop.
-template <typename T, int KM> struct Recent {
-    int s[KM];
-    T x[KM], y[KM], z[KM];
-    int cnt;
-    __device__ __forceinline__ void clear() { cnt = 0; }
-    __device__ __forceinline__ void add(int a, T px, T py, T pz)
-    {
-        s[cnt] = a;
-        x[cnt] = px;
-        y[cnt] = py;
-        z[cnt] = pz;
-        ++cnt;
-    }
-    __device__ __forceinline__ void lookup(int a, T &px, T &py, T &pz) const
-    {
-#pragma unroll
-        for (int q = 0; q < KM; ++q)
-            if (q < cnt && s[q] == a) {
-                px = x[q];
-                py = y[q];
-                pz = z[q];
-            }
-    }
-};
-
 template <typename T, int MEXP, bool SYM>
 __device__ __forceinline__ T pair_du(const Jas<T, MEXP, SYM> &J, T xj, T yj, T zj, T ax, T ay, T az, T bx, T by,
                                      T bz)
@@ -893,8 +867,8 @@ template <int TPW, int K, typename T> __device__ __forceinline__ void group_sum_
 template <typename T, int MEXP, bool SYM, int TPW, int K, int KM, bool GM>
 __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T *sy, T *sz, int n, int nv,
                                            const int (&s)[K], const T (&dx)[K], const T (&dy)[K], const T (&dz)[K],
-                                           const T (&xi)[K], Recent<T, KM> &rec, LogPsiAcc<T> &lp, int &nacc, T *red,
-                                           T *dsm_base, int &ph, int bar_id, int gtid)
+                                           const T (&xi)[K], LogPsiAcc<T> &lp, int &nacc, T *red, T *dsm_base, int &ph,
+                                           int bar_id, int gtid)
 {
     constexpr int VN = Vec<T>::N;
     const T L = J.L;
@@ -904,7 +878,6 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
         ax[i] = sx[s[i]];
         ay[i] = sy[s[i]];
         az[i] = sz[s[i]];
-        rec.lookup(s[i], ax[i], ay[i], az[i]);
         bx[i] = wrap(ax[i] + dx[i], L);
         by[i] = wrap(ay[i] + dy[i], L);
         bz[i] = wrap(az[i] + dz[i], L);
@@ -914,7 +887,6 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
     group_sum_k<TPW, K>(S, red, ph, bar_id, gtid);
     ph ^= 1;
     bool acc[K];
-    rec.clear();
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         T delta = S[i];
@@ -932,15 +904,18 @@ __device__ __forceinline__ bool move_batch(const Jas<T, MEXP, SYM> &J, T *sx, T 
             ++nacc;
         }
     }
+    // Every thread of the group writes every accepted position itself (the same value to the
+    // same address): a thread's later reads of that atom -- as a moved atom of a later batch, or
+    // in its own partner chunks -- see its own write, so no thread can read a position that
+    // another thread has not yet made visible, and the next batch still needs only its one
+    // barrier.  Writes of a batch come after its barrier and before the next batch's barrier, so
+    // they never race with the partner loop's reads.
 #pragma unroll
     for (int i = 0; i < K; ++i)
         if (acc[i]) {
-            if (gtid == (s[i] / VN) % TPW) {
-                sx[s[i]] = bx[i];
-                sy[s[i]] = by[i];
-                sz[s[i]] = bz[i];
-            }
-            rec.add(s[i], bx[i], by[i], bz[i]);
+            sx[s[i]] = bx[i];
+            sy[s[i]] = by[i];
+            sz[s[i]] = bz[i];
         }
     if (TPW == 32) __syncwarp();
     return true;
@@ -1014,8 +989,6 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
     double *A = a.accum + QMC_ACCUM_FIELDS * (size_t)slot;
     int nacc = 0;
     constexpr int K = kb_of<T, TPW>();  // moves per batch
-    Recent<T, K> rec;
-    rec.clear();
     const int lane = gtid & 31;
     const uint32_t wid = d.wid;
     T *dsm = mem.dsm;  // cross terms of a batch
@@ -1076,14 +1049,14 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
                     for (int q = i + 1; q < K; ++q) distinct &= bs[i] != bs[q];
                 bool ok = true;
                 if (distinct) {
-                    ok = move_batch<T, MEXP, SYM, TPW, K, K, GM>(J, sx, sy, sz, n, nv, bs, bdx, bdy, bdz, bxi, rec, lp,
-                                                               nacc, redT, dsm, phT, bar_id, gtid);
+                    ok = move_batch<T, MEXP, SYM, TPW, K, K, GM>(J, sx, sy, sz, n, nv, bs, bdx, bdy, bdz, bxi, lp, nacc,
+                                                               redT, dsm, phT, bar_id, gtid);
                 } else {
                     for (int i = 0; i < K && ok; ++i) {
                         const int s1[1] = {bs[i]};
                         const T x1[1] = {bdx[i]}, y1[1] = {bdy[i]}, z1[1] = {bdz[i]}, c1[1] = {bxi[i]};
-                        ok = move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp,
-                                                                  nacc, redT, dsm, phT, bar_id, gtid);
+                        ok = move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, lp, nacc,
+                                                                  redT, dsm, phT, bar_id, gtid);
                     }
                 }
                 if (!ok) {
@@ -1095,8 +1068,8 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
                 const int s1[1] = {__shfl_sync(FULL, my_s, tt)};
                 const T x1[1] = {__shfl_sync(FULL, mdx, tt)}, y1[1] = {__shfl_sync(FULL, mdy, tt)},
                         z1[1] = {__shfl_sync(FULL, mdz, tt)}, c1[1] = {__shfl_sync(FULL, mxi, tt)};
-                if (!move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, rec, lp, nacc, redT,
-                                                          dsm, phT, bar_id, gtid)) {
+                if (!move_batch<T, MEXP, SYM, TPW, 1, K, GM>(J, sx, sy, sz, n, nv, s1, x1, y1, z1, c1, lp, nacc, redT, dsm,
+                                                          phT, bar_id, gtid)) {
                     if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_RATIO);
                     return false;
                 }
@@ -1104,7 +1077,6 @@ __device__ bool run_range(const SweepArgs &a, const DevWalker &d, GroupMem<T> me
         }
         if (t_stop < n) break;  // the range ends inside this sweep
         group_sync<TPW>(bar_id);
-        rec.clear();
         if (a.recompute_every > 0 && (kk + 1) % (unsigned long long)a.recompute_every == 0) {
             // Eq. (Jastrow) from scratch; the drift of the carried sum (thread 0 carries it) is
             // recorded before it is replaced
@@ -1313,7 +1285,44 @@ struct PassArgs {
     const double *delta;
     int M;
     unsigned *err;
+    // a walker's rows split over `parts` CTAs (row-wise passes of few walkers): CTA part of walker
+    // w stores its share of the outputs in part_out[(w * parts + part) * 8 ..], and the last CTA
+    // of the walker (part_ctr[w]) adds the shares in part order and writes the outputs
+    int parts;
+    double *part_out;
+    unsigned *part_ctr;
 };
+
+// Called by thread 0 of every CTA of a split pass with its share v of the walker's NF outputs
+// (failed: this CTA could not load the walker).  Returns true in the last CTA of the walker to
+// finish, with v holding the sum of all shares in part order, unless some CTA failed; the
+// counter is reset for the next launch.  With one part it returns !failed at once.
+template <int NF>
+__device__ bool combine_parts(const PassArgs &a, int w, int part, double (&v)[NF], bool failed)
+{
+    static_assert(NF <= 7, "eight slots per part: NF outputs and a failure flag");
+    if (a.parts == 1) return !failed;
+    double *base = a.part_out + (size_t)w * a.parts * 8;
+    double *slot = base + (size_t)part * 8;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) slot[f] = v[f];
+    slot[7] = failed ? 1.0 : 0.0;
+    __threadfence();
+    const unsigned prev = atomicAdd(a.part_ctr + w, 1u);
+    if (prev != (unsigned)(a.parts - 1)) return false;
+    __threadfence();
+    bool bad = false;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) v[f] = 0.0;
+    for (int p = 0; p < a.parts; ++p) {
+        const volatile double *q = base + (size_t)p * 8;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) v[f] += q[f];
+        bad |= q[7] != 0.0;
+    }
+    a.part_ctr[w] = 0u;
+    return !bad;
+}
 
 // kind: 0 = local energy (5 outputs), 1 = ln psi (1 output)
 template <typename T, int MEXP, bool SYM, int TPW>
@@ -1324,7 +1333,8 @@ __global__ void __launch_bounds__(TPW) pass_kernel(PassArgs a, int kind)
     mem.bind(smem, a.stride, TPW, a.tile && kind == 0);
     T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
     double *redD = mem.redD;
-    const DevWalker d = a.walkers[blockIdx.x];
+    const int w = blockIdx.x / a.parts, part = blockIdx.x % a.parts;  // walker, share of its rows
+    const DevWalker d = a.walkers[w];
     const int gtid = threadIdx.x;
     int phT = 0, phD = 0;
     constexpr int VN = Vec<T>::N;
@@ -1337,7 +1347,11 @@ __global__ void __launch_bounds__(TPW) pass_kernel(PassArgs a, int kind)
     }
     if (!(a.gmem ? check_walker<T, TPW>(gx, d.n, d.pad, (T)d.L, redT, phT, 1, gtid)
                  : load_walker<T, TPW>(gx, d.n, d.pad, a.stride, (T)d.L, sx, sy, sz, redT, phT, 1, gtid))) {
-        if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
+        if (gtid == 0) {
+            atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
+            double none[5] = {};
+            combine_parts<5>(a, w, part, none, true);  // the walker's other parts must not wait for it
+        }
         return;
     }
     Jas<T, MEXP, SYM> J;
@@ -1346,19 +1360,19 @@ __global__ void __launch_bounds__(TPW) pass_kernel(PassArgs a, int kind)
     if (kind == 0) {
         double e[5];
         if constexpr (std::is_same<T, float>::value) {
-            if (a.tile)
+            if (a.tile)  // the tiled pass is never split (parts == 1)
                 group_energy_tiled<MEXP, SYM, TPW>(J, sx, sy, sz, mem.fx, mem.fy, mem.fz, d.n, a.h2m, redD, phD, 1,
                                                    gtid, e);
             else
-                group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, d.n, nv, a.h2m, redD, phD, 1, gtid, e);
+                group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, d.n, nv, a.h2m, redD, phD, 1, gtid, e, part, a.parts);
         } else {
-            group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, d.n, nv, a.h2m, redD, phD, 1, gtid, e);
+            group_energy<T, MEXP, SYM, TPW>(J, sx, sy, sz, d.n, nv, a.h2m, redD, phD, 1, gtid, e, part, a.parts);
         }
-        if (gtid == 0)
+        if (gtid == 0 && combine_parts<5>(a, w, part, e, false))
             for (int q = 0; q < 5; ++q) a.out[5 * (size_t)d.slot + q] = e[q];
     } else {
-        const double lp = group_log_psi<T, MEXP, SYM, TPW>(J, sx, sy, sz, d.n, nv, redD, phD, 1, gtid);
-        if (gtid == 0) a.out[d.slot] = lp;
+        double lp[1] = {group_log_psi<T, MEXP, SYM, TPW>(J, sx, sy, sz, d.n, nv, redD, phD, 1, gtid, part, a.parts)};
+        if (gtid == 0 && combine_parts<1>(a, w, part, lp, false)) a.out[d.slot] = lp[0];
     }
 }
 
@@ -1427,7 +1441,8 @@ __global__ void __launch_bounds__(TPW) hist_kernel(PassArgs a, int nbins, double
     mem.bind(smem, a.stride, TPW, false);
     unsigned *counts = reinterpret_cast<unsigned *>(smem + group_smem<T>(a.stride, TPW, false));
     T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
-    const DevWalker d = a.walkers[blockIdx.x];
+    const int part = blockIdx.x % a.parts;  // share of the walker's rows (counts add exactly)
+    const DevWalker d = a.walkers[blockIdx.x / a.parts];
     const int gtid = threadIdx.x;
     int phT = 0;
     constexpr int VN = Vec<T>::N;
@@ -1449,7 +1464,7 @@ __global__ void __launch_bounds__(TPW) hist_kernel(PassArgs a, int nbins, double
     __syncthreads();
     const int n = d.n, nv = (n + VN - 1) / VN;
     const T r2max = (T)(rmax * rmax), scale = (T)((double)nbins / rmax);
-    for (int i = gtid; i < n; i += TPW) {
+    for (int i = part * TPW + gtid; i < n; i += a.parts * TPW) {
         const T xi = sx[i], yi = sy[i], zi = sz[i];
         for (int c = 0; c < nv; ++c) {
             const V X = reinterpret_cast<const V *>(sx)[c];
@@ -1475,7 +1490,12 @@ __global__ void __launch_bounds__(TPW) hist_kernel(PassArgs a, int nbins, double
     }
     __syncthreads();
     unsigned long long *h = hist + (size_t)d.slot * nbins;
-    for (int b = gtid; b < nbins; b += TPW) h[b] += counts[b];
+    if (a.parts == 1) {
+        for (int b = gtid; b < nbins; b += TPW) h[b] += counts[b];
+    } else {  // several CTAs add to the walker's row: integer atomics, exact in any order
+        for (int b = gtid; b < nbins; b += TPW)
+            if (counts[b]) atomicAdd(h + b, (unsigned long long)counts[b]);
+    }
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -1491,7 +1511,8 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
     mem.bind(smem, a.stride, TPW, false);
     T *sx = mem.sx, *sy = mem.sy, *sz = mem.sz, *redT = mem.redT;
     double *redD = mem.redD;
-    const DevWalker d = a.walkers[blockIdx.x];
+    const int w = blockIdx.x / a.parts, part = blockIdx.x % a.parts;  // walker, share of its rows
+    const DevWalker d = a.walkers[w];
     const int gtid = threadIdx.x;
     int phT = 0, phD = 0;
     constexpr int VN = Vec<T>::N;
@@ -1506,7 +1527,11 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
     }
     if (!(a.gmem ? check_walker<T, TPW>(gx, d.n, d.pad, L, redT, phT, 1, gtid)
                  : load_walker<T, TPW>(gx, d.n, d.pad, a.stride, L, sx, sy, sz, redT, phT, 1, gtid))) {
-        if (gtid == 0) atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
+        if (gtid == 0) {
+            atomicOr(a.err, QMC_DEVERR_NONFINITE_POS);
+            double none[6] = {};
+            combine_parts<6>(a, w, part, none, true);  // the walker's other parts must not wait for it
+        }
         return;
     }
     const int n = d.n, nv = (n + VN - 1) / VN;
@@ -1516,7 +1541,7 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
     const T Km = (T)(d.K * ::log(d.b > 0 ? 2.0 * d.b / d.L : 1.0));
     const T c1 = (T)1 / m, c2 = (T)(2.0 * d.m + 1.0) / (m * (m + (T)1));
     double sLp = 0, sLpm = 0, sV = 0, sLap = 0, sLapm = 0, sF2 = 0, sFFm = 0;
-    for (int i = gtid; i < n; i += TPW) {
+    for (int i = part * TPW + gtid; i < n; i += a.parts * TPW) {  // this CTA's share of the rows
         const T xi = sx[i], yi = sy[i], zi = sz[i];
         RowSum<T> a_lp, a_lpm, a_v, a_lap, a_lapm, a_fx, a_fy, a_fz, a_gx, a_gy, a_gz;
         for (int c0 = 0; c0 < nv; c0 += row_block<T>()) {
@@ -1597,13 +1622,11 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
     if (gtid == 0) {
         const double k = 0.5 * a.h2m;
         const double mb = d.b > 0 ? d.m / d.b : 0.0;  // (dc/db)/c
-        double *o = a.out + 6 * (size_t)d.slot;
-        o[0] = 0.5 * sLp;
-        o[1] = 0.5 * sV - k * (sLap + sF2);
-        o[2] = mb * 0.5 * sLp;
-        o[3] = 0.5 * sLpm;
-        o[4] = -k * mb * (sLap + 2.0 * sF2);
-        o[5] = -k * (sLapm + 2.0 * sFFm);
+        // every output is linear in the row sums, so the shares of a split walker add up
+        double o[6] = {0.5 * sLp, 0.5 * sV - k * (sLap + sF2), mb * 0.5 * sLp, 0.5 * sLpm, -k * mb * (sLap + 2.0 * sF2),
+                       -k * (sLapm + 2.0 * sFFm)};
+        if (combine_parts<6>(a, w, part, o, false))
+            for (int q = 0; q < 6; ++q) a.out[6 * (size_t)d.slot + q] = o[q];
     }
 }
 

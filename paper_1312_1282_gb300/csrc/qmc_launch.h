@@ -50,7 +50,7 @@ cudaError_t launch_init(int precision, int grid, size_t smem, cudaStream_t st, c
 
 // calibration probes (qmc_probe_rates): launcher, resident CTAs per SM, work per thread and loop
 // iteration (lane operations, or pair evaluations for the pair probe)
-cudaError_t launch_probe(int kind, int grid, int threads, int iters, long long *cycles, float *sink, cudaStream_t st);
+cudaError_t launch_probe(int kind, int grid, int threads, int iters, float *sink, cudaStream_t st);
 cudaError_t probe_occupancy(int kind, int threads, int *blocks);
 double probe_ops_per_thread_iter(int kind);
 

@@ -145,9 +145,10 @@ def test_resume_is_bitwise_identical():
         torch.cuda.synchronize()
         assert torch.equal(A.pos, B.pos) and torch.equal(la, lb) and torch.equal(sa, sb)
         assert torch.equal(aa[:, :8], ab[:, :8])
-        # the ln psi drift (fields 8, 9) measures the rounding of the carried sum, which a call
-        # boundary rounds once more (to the stored double): equal to that rounding
-        np.testing.assert_allclose(aa[:, 8:].cpu().numpy(), ab[:, 8:].cpu().numpy(), rtol=0, atol=1e-9)
+        # the ln psi drift (fields 8, 9) measures the rounding of the carried sum; a call boundary
+        # collapses its compensated-float part into the stored double once more, which moves it by
+        # the rounding of that FP32 sum (here the drift also holds the start's ln psi, left at 0)
+        np.testing.assert_allclose(aa[:, 8:].cpu().numpy(), ab[:, 8:].cpu().numpy(), rtol=1e-6, atol=1e-9)
 
 
 def test_autotune_keeps_the_chain():

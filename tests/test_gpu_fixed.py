@@ -231,3 +231,29 @@ def test_pair_correlation_of_a_liquid():
     assert np.all(g[r < 1.8] == 0.0)           # hard core of the Jastrow factor
     assert 1.2 < g.max() < 1.8 and 3.0 < r[np.argmax(g)] < 4.0   # first shell of liquid 4He
     assert abs(g[(r > 9) & (r < 12)].mean() - 1.0) < 0.05
+
+
+def test_split_passes_match_oracle():
+    # Two walkers of N = 2048 in FP64: with far fewer walkers than SMs every row-wise pass splits
+    # each walker's rows over several CTAs, whose shares the last CTA of the walker adds up (ln psi,
+    # local energy, adjoint) or which add their counts atomically (histogram).
+    P = lattice_batch([2048, 2044], q.QMC_FP64, seed=90)
+    opt = q.options(precision=q.QMC_FP64)
+    lp, e, g = zeros(P.W), zeros((P.W, 5)), zeros((P.W, 6))
+    nbins = 50
+    hist = zeros((P.W, nbins), torch.int64)
+    for _ in range(2):  # the second call of each pass finds the counters reset by the first
+        q.qmc_log_psi(P.d, opt, P.pos, lp)
+        q.qmc_local_energy(P.d, opt, P.pos, e)
+        q.qmc_energy_grad(P.d, opt, P.pos, g)
+    rmax = min(P.Ls) / 2
+    q.qmc_pair_hist(P.d, opt, P.pos, nbins, rmax, hist)
+    assert q.qmc_status(timeout_ms=120000) == 0
+    for w in range(P.W):
+        c, L, b = P.confs[w], P.Ls[w], P.bs[w]
+        _close(lp.cpu().numpy()[w], oracle.log_psi(c, L, b), 1e-10)
+        want = oracle.local_energy(c, L, b, 5.0, 1, H2M)
+        _close(e.cpu().numpy()[w], want, 1e-10, energy_scale(want))
+        wg = oracle.energy_grad(c, L, b, 5.0, 1, H2M)
+        _close(g.cpu().numpy()[w], wg, 1e-10, grad_scales(c, L, b, 5.0, 1, H2M, rows=64))
+        assert np.array_equal(hist.cpu().numpy()[w], oracle.pair_hist(c, L, nbins, rmax).astype(np.int64))
