@@ -39,11 +39,11 @@ METRIC = "pair evals/s and sweeps/s at N=1952, FP32-batched vs FP64 plain, E/ato
 WORKLOAD = "VMC liquid 4He N=1952 rho=0.02186 b=3.07 m=5 Aziz-II, 528 walkers, 5 sweeps + 1 local energy per step"
 # FP32 operations per pair evaluation of a move (difference 3, image fold 6, r^2 3, clamp 1,
 # r and L - r 2, q^2 q^4 w^2 w^4 4, two fused multiply-accumulates 2) and per unordered pair of
-# the local-energy pass (difference 3, signed image 12, r^2 3, mask 1, f, f', f'' 9, the f(L - r)
-# terms 10, drift and its row/column sums 10, Laplacian term 3, Aziz II 16: 71).  SFU operations
-# (2 and 3-4) are not counted.
+# the local-energy pass (difference 3, signed image 9, r^2 3, mask 1, r and L - r 2, the powers
+# q^2 q^4 q^6 w^2 w^4 w^6 6, drift g (r_i - r_j) with its row and column sums 11, Laplacian term
+# and its sum 5, Aziz II 8: 48).  SFU operations (2 and 3-4) and selects are not counted.
 C_PAIR = 21.0
-C_ENERGY = 71.0
+C_ENERGY = 48.0
 FP32_LANES_PER_SM = 128
 SFU_PAIR, SFU_ENERGY, SFU_LANES_PER_SM = 2.0, 3.0, 16
 

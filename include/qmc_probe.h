@@ -22,8 +22,9 @@ extern "C" {
 #define QMC_PROBE_RSQRT 3     /* SFU reciprocal square root (rsqrt.approx.ftz.f32) */
 #define QMC_PROBE_DFMA 4      /* FP64 fused multiply-add (fma.rn.f64) */
 #define QMC_PROBE_PAIR 5      /* the sweep's FP32 partner arithmetic alone (Eqs. JastrowUpdate,
-                                 uFunction, fifthPower with exponent 5): two moves, old and new
-                                 position, four partners per shared-memory chunk, no reduction */
+                                 uFunction, fifthPower with exponent 5): two moves, each with its
+                                 old and new position in one f32x2, four partners per
+                                 shared-memory chunk, no reduction */
 #define QMC_PROBE_COUNT 6
 
 /*
@@ -31,9 +32,10 @@ extern "C" {
  * threads (a multiple of 32, 32..1024; the pair probe at most 512) for `iters` loop iterations
  * (1..1e6) on `stream`, after a short warm-up launch, and time it with CUDA events; the rate is
  * the operations of all CTAs over the elapsed time and the SM count (the CTAs are spread evenly,
- * all resident at once; fewer per SM if the kernel's occupancy is lower).  Eight (pair probe:
- * four) independent dependency chains per thread; the operations are inline PTX on values that
- * change every iteration, so none is folded away or hoisted out of the loop.
+ * all resident at once; fewer per SM if the kernel's occupancy is lower).  Eight independent
+ * dependency chains per thread (pair probe: one accumulator per move, eight independent pair
+ * evaluations per chunk); the operations are inline PTX (pair probe: packed f32x2 intrinsics) on
+ * values that change every iteration, so none is folded away or hoisted out of the loop.
  *   out    host array of QMC_PROBE_COUNT doubles, written on success.
  * Allocates and frees a small device buffer, synchronises the stream.  Returns QMC_OK, QMC_ERR_ARG
  * for out-of-range arguments or QMC_ERR_CUDA.  Not for use during stream capture.

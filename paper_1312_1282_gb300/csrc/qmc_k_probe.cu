@@ -90,34 +90,30 @@ __global__ void __launch_bounds__(512) pair_probe_kernel(int iters, float *sink)
     Packed5 P;
     P.init(J);
     const float a0 = 0.37f * L + 1e-3f * (threadIdx.x & 31), a1 = 0.61f * L;
-    float2 acco0 = make_float2(0.f, 0.f), accn0 = acco0, acco1 = acco0, accn1 = acco0;
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
     __syncthreads();
     for (int it = 0; it < iters; ++it) {
         // the moved positions (all three coordinates) and the partners a thread reads change with
-        // the iteration, so no part of the loop body is invariant
+        // the iteration, so no part of the loop body is invariant; as in the sweep, each move packs
+        // its old and new position in one f32x2 and every partner is duplicated into both lanes
         const float e = 1e-3f * (float)(it & 15);
-        const float2 nax0 = make_float2(-(a0 + e), -(a0 + e)), nbx0 = make_float2(-(a0 + 0.5f), -(a0 + 0.5f));
-        const float2 nax1 = make_float2(-(a1 - e), -(a1 - e)), nbx1 = make_float2(-(a1 - 0.4f), -(a1 - 0.4f));
-        const float2 ny = make_float2(-(0.5f * L + e), -(0.5f * L + e)), nz = make_float2(-(0.25f * L - e), -(0.25f * L - e));
+        const float2 px0 = make_float2(a0 + e, a0 + 0.5f), px1 = make_float2(a1 - e, a1 - 0.4f);
+        const float2 py0 = make_float2(0.5f * L + e, 0.5f * L - e), py1 = make_float2(0.3f * L - e, 0.3f * L + e);
+        const float2 pz0 = make_float2(0.25f * L - e, 0.25f * L), pz1 = make_float2(0.75f * L, 0.75f * L + e);
         const int rot = it % nv;
         for (int c0 = threadIdx.x; c0 < nv; c0 += blockDim.x) {
             const int c = c0 + rot < nv ? c0 + rot : c0 + rot - nv;
             const float4 X = part[c], Y = part[nv + c], Z = part[2 * nv + c];
-            const float2 xa = make_float2(X.x, X.y), xb = make_float2(X.z, X.w);
-            const float2 ya = make_float2(Y.x, Y.y), yb = make_float2(Y.z, Y.w);
-            const float2 za = make_float2(Z.x, Z.y), zb = make_float2(Z.z, Z.w);
-            P.acc5(__fadd2_rn(xa, nax0), __fadd2_rn(ya, ny), __fadd2_rn(za, nz), acco0);
-            P.acc5(__fadd2_rn(xa, nbx0), __fadd2_rn(ya, ny), __fadd2_rn(za, nz), accn0);
-            P.acc5(__fadd2_rn(xb, nax0), __fadd2_rn(yb, ny), __fadd2_rn(zb, nz), acco0);
-            P.acc5(__fadd2_rn(xb, nbx0), __fadd2_rn(yb, ny), __fadd2_rn(zb, nz), accn0);
-            P.acc5(__fadd2_rn(xa, nax1), __fadd2_rn(ya, ny), __fadd2_rn(za, nz), acco1);
-            P.acc5(__fadd2_rn(xa, nbx1), __fadd2_rn(ya, ny), __fadd2_rn(za, nz), accn1);
-            P.acc5(__fadd2_rn(xb, nax1), __fadd2_rn(yb, ny), __fadd2_rn(zb, nz), acco1);
-            P.acc5(__fadd2_rn(xb, nbx1), __fadd2_rn(yb, ny), __fadd2_rn(zb, nz), accn1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float xe = Vec<float>::get(X, k), ye = Vec<float>::get(Y, k), ze = Vec<float>::get(Z, k);
+                const float2 xj = make_float2(xe, xe), yj = make_float2(ye, ye), zj = make_float2(ze, ze);
+                P.acc5(__ffma2_rn(px0, P.m1, xj), __ffma2_rn(py0, P.m1, yj), __ffma2_rn(pz0, P.m1, zj), acc0);
+                P.acc5(__ffma2_rn(px1, P.m1, xj), __ffma2_rn(py1, P.m1, yj), __ffma2_rn(pz1, P.m1, zj), acc1);
+            }
         }
     }
-    sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] =
-        acco0.x + acco0.y + accn0.x + accn0.y + acco1.x + acco1.y + accn1.x + accn1.y;
+    sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = acc0.x + acc0.y + acc1.x + acc1.y;
 }
 
 size_t probe_smem(int kind, int threads);

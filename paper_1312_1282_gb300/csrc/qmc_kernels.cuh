@@ -423,33 +423,42 @@ template <int MEXP, bool SYM> struct TilePair {
 
 // Two tile steps at once (partners j0 and j1 of the same row atom), packed f32x2 arithmetic for
 // exponent 5 and the symmetrised u; the general case evaluates the scalar form twice.
+// In the packed form the Jastrow terms come out divided by constants that the caller applies
+// once per walker: with A = q^6, B = w^6 (q = 1/r, w = 1/(L - r)), u'(r) = 5c (B - A) and
+// u''(r) = 30c (A q + B w), so the drift g (r_i - r_j) is returned over GSCALE = 5c and the
+// Laplacian term u'' + 2u'/r = 10c [q (B + 2A) + 3 B w] over LSCALE = 10c.  The Aziz II
+// potential reuses the powers: eps F C_2k / x^2k = F A (k6 + k8 q^2 + k10 q^4) with the
+// constants rm^2k eps C_2k, and eps A* exp(-alpha x + beta x^2) = 2^(e0 + ea r + eb r^2).
 template <int MEXP, bool SYM> struct TilePair2 {
+    static constexpr bool PACKED = MEXP == 5 && SYM;
     TilePair<MEXP, SYM> P;
-    float2 L2, iL2, nL2, M2, nM2, m1, c2, nm2, m2, mm12, two2, irm2, rm2sq, C6, C8, C10, beta2, nalpha2, l2e2, A2, eps2;
+    float GSCALE, LSCALE;
+    float2 L2, iL2, nL2, M2, nM2, m1, two2, three2, k6, k8, k10, e0, ea, eb;
     __device__ __forceinline__ TilePair2(const Jas<float, MEXP, SYM> &j) : P(j)
     {
-        const float rm = 2.963f;
+        // Aziz II (HFD-B(HE)) parameters, folded in double and rounded once
+        const double eps = 10.948, rm = 2.963, A = 1.8443101e5, alpha = 10.43329537, beta = -2.27965105,
+                     C6 = 1.36745214, C8 = 0.42123807, C10 = 0.17473318, log2e = 1.4426950408889634;
+        const double rm2 = rm * rm, rm6 = rm2 * rm2 * rm2;
+        GSCALE = PACKED ? 5.f * j.c : 1.f;
+        LSCALE = PACKED ? 10.f * j.c : 1.f;
         L2 = make_float2(j.L, j.L);
         iL2 = make_float2(1.f / j.L, 1.f / j.L);
         nL2 = make_float2(-j.L, -j.L);
         M2 = make_float2(12582912.f, 12582912.f);
         nM2 = make_float2(-12582912.f, -12582912.f);
         m1 = make_float2(-1.f, -1.f);
-        c2 = make_float2(j.c, j.c);
-        nm2 = make_float2(-j.m, -j.m);
-        m2 = make_float2(j.m, j.m);
-        mm12 = make_float2(j.m * (j.m + 1.f), j.m * (j.m + 1.f));
         two2 = make_float2(2.f, 2.f);
-        irm2 = make_float2(1.f / rm, 1.f / rm);
-        rm2sq = make_float2(rm * rm, rm * rm);
-        C6 = make_float2(1.36745214f, 1.36745214f);
-        C8 = make_float2(0.42123807f, 0.42123807f);
-        C10 = make_float2(0.17473318f, 0.17473318f);
-        beta2 = make_float2(-2.27965105f, -2.27965105f);
-        nalpha2 = make_float2(-10.43329537f, -10.43329537f);
-        l2e2 = make_float2(1.4426950408889634f, 1.4426950408889634f);
-        A2 = make_float2(1.8443101e5f, 1.8443101e5f);
-        eps2 = make_float2(10.948f, 10.948f);
+        three2 = make_float2(3.f, 3.f);
+        const float f6 = (float)(eps * C6 * rm6), f8 = (float)(eps * C8 * rm6 * rm2),
+                    f10 = (float)(eps * C10 * rm6 * rm2 * rm2);
+        const float fe0 = (float)log2(eps * A), fea = (float)(-alpha * log2e / rm), feb = (float)(beta * log2e / rm2);
+        k6 = make_float2(f6, f6);
+        k8 = make_float2(f8, f8);
+        k10 = make_float2(f10, f10);
+        e0 = make_float2(fe0, fe0);
+        ea = make_float2(fea, fea);
+        eb = make_float2(feb, feb);
     }
     __device__ __forceinline__ float2 mi(float2 d) const
     {
@@ -460,7 +469,7 @@ template <int MEXP, bool SYM> struct TilePair2 {
                                                bool take0, bool take1, float2 &gx, float2 &gy, float2 &gz,
                                                float2 &lap, float2 &v) const
     {
-        if constexpr (MEXP == 5 && SYM) {
+        if constexpr (PACKED) {
             const float2 dx = mi(__ffma2_rn(xj, m1, make_float2(xi, xi)));
             const float2 dy = mi(__ffma2_rn(yj, m1, make_float2(yi, yi)));
             const float2 dz = mi(__ffma2_rn(zj, m1, make_float2(zi, zi)));
@@ -471,37 +480,32 @@ template <int MEXP, bool SYM> struct TilePair2 {
             const float2 q = make_float2(rsqrt_a(r2.x), rsqrt_a(r2.y));
             const float2 r = __fmul2_rn(r2, q);
             const float2 q2 = __fmul2_rn(q, q);
-            const float2 f0 = __fmul2_rn(c2, __fmul2_rn(__fmul2_rn(q2, q2), q));
-            float2 u1 = __fmul2_rn(__fmul2_rn(nm2, f0), q);
-            float2 u2 = __fmul2_rn(__fmul2_rn(mm12, f0), q2);
+            const float2 q4 = __fmul2_rn(q2, q2);
+            const float2 A = __fmul2_rn(q4, q2);
             const float2 w = __ffma2_rn(r, m1, L2);
             const float2 iw = make_float2(rcp_a(w.x), rcp_a(w.y));
             const float2 w2 = __fmul2_rn(iw, iw);
-            const float2 g0 = __fmul2_rn(c2, __fmul2_rn(__fmul2_rn(w2, w2), iw));
-            u1 = __ffma2_rn(__fmul2_rn(m2, g0), iw, u1);
-            u2 = __ffma2_rn(__fmul2_rn(mm12, g0), w2, u2);
-            float2 g = __fmul2_rn(u1, q);
+            const float2 B = __fmul2_rn(__fmul2_rn(w2, w2), w2);
+            float2 g = __fmul2_rn(__ffma2_rn(A, m1, B), q);  // u'/r over 5c
             g = make_float2(ok0 ? g.x : 0.f, ok1 ? g.y : 0.f);
             gx = __fmul2_rn(g, dx);
             gy = __fmul2_rn(g, dy);
             gz = __fmul2_rn(g, dz);
-            const float2 lp = __ffma2_rn(__fmul2_rn(two2, u1), q, u2);
+            const float2 lp = __ffma2_rn(__ffma2_rn(A, two2, B), q, __fmul2_rn(B, __fmul2_rn(iw, three2)));
             lap = make_float2(ok0 ? lp.x : 0.f, ok1 ? lp.y : 0.f);
-            // Aziz II; the damping factor only where some lane has x < D
-            const float2 x = __fmul2_rn(r, irm2);
-            const float2 y = __fmul2_rn(q2, rm2sq);
-            const float2 disp = __fmul2_rn(__fmul2_rn(__fmul2_rn(y, y), y), __ffma2_rn(__ffma2_rn(C10, y, C8), y, C6));
-            const float2 ea = __fmul2_rn(__fmul2_rn(x, __ffma2_rn(beta2, x, nalpha2)), l2e2);
-            const float2 rep = __fmul2_rn(A2, make_float2(ex2_a(ea.x), ex2_a(ea.y)));
-            float2 F = make_float2(1.f, 1.f);
-            const float D = 1.4826f;
-            const bool d0 = ok0 && x.x < D, d1 = ok1 && x.y < D;
+            // Aziz II; the damping factor F = exp(-(D/x - 1)^2) only where some lane has x < D
+            const float2 disp = __fmul2_rn(A, __ffma2_rn(__ffma2_rn(k10, q2, k8), q2, k6));
+            const float2 ex = __ffma2_rn(eb, r2, __ffma2_rn(ea, r, e0));
+            const float2 rep = make_float2(ex2_a(ex.x), ex2_a(ex.y));
+            float2 nF = m1;
+            const float Drm = 1.4826f * 2.963f;  // x < D is r < D rm
+            const bool d0 = ok0 && r.x < Drm, d1 = ok1 && r.y < Drm;
             if (__any_sync(FULL, d0 || d1)) {
-                const float t0 = fmaf(D * 2.963f, q.x, -1.f), t1 = fmaf(D * 2.963f, q.y, -1.f);
-                F.x = d0 ? Fn<float>::exp(-(t0 * t0)) : 1.f;
-                F.y = d1 ? Fn<float>::exp(-(t1 * t1)) : 1.f;
+                const float t0 = fmaf(Drm, q.x, -1.f), t1 = fmaf(Drm, q.y, -1.f);
+                nF.x = d0 ? -Fn<float>::exp(-(t0 * t0)) : -1.f;
+                nF.y = d1 ? -Fn<float>::exp(-(t1 * t1)) : -1.f;
             }
-            const float2 vv = __fmul2_rn(eps2, __ffma2_rn(__fmul2_rn(F, m1), disp, rep));
+            const float2 vv = __ffma2_rn(nF, disp, rep);
             v = make_float2(ok0 ? vv.x : 0.f, ok1 ? vv.y : 0.f);
         } else {
             P(xi, yi, zi, xj.x, yj.x, zj.x, take0, gx.x, gy.x, gz.x, lap.x, v.x);
@@ -519,6 +523,7 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
     const int lane = gtid & 31, warp = gtid >> 5;
     const int NB = (n + 31) >> 5;
     const TilePair2<MEXP, SYM> P2(J);
+    const float2 z2 = make_float2(0.f, 0.f);
     for (int i = gtid; i < NB * 32; i += TPW) {
         Fx[i] = 0.f;
         Fy[i] = 0.f;
@@ -534,18 +539,19 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
             if (a >= NB || b >= NB) continue;  // the dummy block
             const int i = 32 * a + lane;
             const float xi = sx[i], yi = sy[i], zi = sz[i];
-            float rx = 0.f, ry = 0.f, rz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, lap = 0.f, v = 0.f;
+            float2 rx = z2, ry = z2, rz = z2, lap = z2, v = z2;
+            float cx = 0.f, cy = 0.f, cz = 0.f;
             const int src = (lane + 1) & 31;
             for (int t = 0; t < 32; t += 2) {
                 const int j0 = 32 * b + ((lane + t) & 31), j1 = 32 * b + ((lane + t + 1) & 31);
                 float2 gx, gy, gz, l2, v2;
                 P2(xi, yi, zi, make_float2(sx[j0], sx[j1]), make_float2(sy[j0], sy[j1]), make_float2(sz[j0], sz[j1]),
                    true, true, gx, gy, gz, l2, v2);
-                rx += gx.x + gx.y;
-                ry += gy.x + gy.y;
-                rz += gz.x + gz.y;
-                lap += l2.x + l2.y;
-                v += v2.x + v2.y;
+                rx = __fadd2_rn(rx, gx);
+                ry = __fadd2_rn(ry, gy);
+                rz = __fadd2_rn(rz, gz);
+                lap = __fadd2_rn(lap, l2);
+                v = __fadd2_rn(v, v2);
                 // partner drift: step t belongs to the register now here, step t+1 to the next one
                 cx = __shfl_sync(FULL, cx - gx.x, src) - gx.y;
                 cy = __shfl_sync(FULL, cy - gy.x, src) - gy.y;
@@ -554,33 +560,34 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
                 cy = __shfl_sync(FULL, cy, src);
                 cz = __shfl_sync(FULL, cz, src);
             }
-            Fx[i] += rx;
-            Fy[i] += ry;
-            Fz[i] += rz;
+            Fx[i] += rx.x + rx.y;
+            Fy[i] += ry.x + ry.y;
+            Fz[i] += rz.x + rz.y;
             const int jb = 32 * b + lane;
             Fx[jb] += cx;
             Fy[jb] += cy;
             Fz[jb] += cz;
-            kV.add(v);
-            kLap.add(lap);
+            kV.add(v.x + v.y);
+            kLap.add(lap.x + lap.y);
         }
         group_sync<TPW>(bar_id);
     }
     for (int b = warp; b < NB; b += NW) {  // pairs inside one block: steps 1..15, and 16 for half the lanes
         const int i = 32 * b + lane;
         const float xi = sx[i], yi = sy[i], zi = sz[i];
-        float rx = 0.f, ry = 0.f, rz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, lap = 0.f, v = 0.f;
+        float2 rx = z2, ry = z2, rz = z2, lap = z2, v = z2;
+        float cx = 0.f, cy = 0.f, cz = 0.f;
         const int src1 = (lane + 1) & 31;
         for (int t = 1; t <= 16; t += 2) {
             const int j0 = 32 * b + ((lane + t) & 31), j1 = 32 * b + ((lane + t + 1) & 31);
             float2 gx, gy, gz, l2, v2;
             P2(xi, yi, zi, make_float2(sx[j0], sx[j1]), make_float2(sy[j0], sy[j1]), make_float2(sz[j0], sz[j1]),
                true, t + 1 < 16 || lane < 16, gx, gy, gz, l2, v2);
-            rx += gx.x + gx.y;
-            ry += gy.x + gy.y;
-            rz += gz.x + gz.y;
-            lap += l2.x + l2.y;
-            v += v2.x + v2.y;
+            rx = __fadd2_rn(rx, gx);
+            ry = __fadd2_rn(ry, gy);
+            rz = __fadd2_rn(rz, gz);
+            lap = __fadd2_rn(lap, l2);
+            v = __fadd2_rn(v, v2);
             cx = __shfl_sync(FULL, cx - gx.x, src1) - gx.y;  // step t, then step t+1
             cy = __shfl_sync(FULL, cy - gy.x, src1) - gy.y;
             cz = __shfl_sync(FULL, cz - gz.x, src1) - gz.y;
@@ -595,18 +602,19 @@ __device__ void group_energy_tiled(const Jas<float, MEXP, SYM> &J, const float *
         cx = __shfl_sync(FULL, cx, src);
         cy = __shfl_sync(FULL, cy, src);
         cz = __shfl_sync(FULL, cz, src);
-        Fx[i] += rx + cx;
-        Fy[i] += ry + cy;
-        Fz[i] += rz + cz;
-        kV.add(v);
-        kLap.add(lap);
+        Fx[i] += (rx.x + rx.y) + cx;
+        Fy[i] += (ry.x + ry.y) + cy;
+        Fz[i] += (rz.x + rz.y) + cz;
+        kV.add(v.x + v.y);
+        kLap.add(lap.x + lap.y);
     }
     group_sync<TPW>(bar_id);
     double sF2 = 0.0;
     for (int i = gtid; i < n; i += TPW) sF2 += (double)Fx[i] * Fx[i] + (double)Fy[i] * Fy[i] + (double)Fz[i] * Fz[i];
     double sV = group_sum<TPW>(kV.value(), redD, phD, bar_id, gtid);
-    double sLap = 2.0 * group_sum<TPW>(kLap.value(), redD, phD, bar_id, gtid);  // each pair's term belongs to both atoms
-    sF2 = group_sum<TPW>(sF2, redD, phD, bar_id, gtid);
+    // each pair's term belongs to both atoms; the packed pair form leaves the constant factors out
+    double sLap = 2.0 * (double)P2.LSCALE * group_sum<TPW>(kLap.value(), redD, phD, bar_id, gtid);
+    sF2 = (double)P2.GSCALE * (double)P2.GSCALE * group_sum<TPW>(sF2, redD, phD, bar_id, gtid);
     const double k = 0.5 * h2m;
     out[0] = sV;
     out[1] = -k * (sLap + sF2);
@@ -751,6 +759,12 @@ __device__ __forceinline__ T pair_du(const Jas<T, MEXP, SYM> &J, T xj, T yj, T z
     return J.u(fma(qx, qx, fma(qy, qy, qz * qz))) - J.u(fma(px, px, fma(py, py, pz * pz)));
 }
 
+// The FP32 sweep with exponent 5 and the symmetrised u runs the packed partner loop (Packed5)
+template <typename T, int MEXP, bool SYM> constexpr bool packed5()
+{
+    return std::is_same<T, float>::value && MEXP == 5 && SYM;
+}
+
 // This thread's partner sums S[0..K-1] of one batch; the owners of the moved atoms' chunks
 // also write the cross terms D_ik (i > k) to dsm[i * K + k].  In the partner loop every moved
 // atom is replaced by NaN, which contributes exactly zero to every sum (the clamp), so the loop
@@ -770,20 +784,18 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
         cs[i] = s[i] / VN;
         S[i] = (T)0;
     }
-    if constexpr (std::is_same<T, float>::value && MEXP == 5 && SYM) {
+    if constexpr (packed5<T, MEXP, SYM>()) {
         Packed5 P;
         P.init(J);
-        float2 nax[K], nay[K], naz[K], nbx[K], nby[K], nbz[K], acco[K], accn[K];
+        // one f32x2 lane pair per move: (old, new) position, and acc = (sum at a_i, sum at b_i);
+        // the difference r_j - p is taken as fma(p, -1, r_j), the exactly rounded r_j - p
+        float2 px[K], py[K], pz[K], acc[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-            nax[i] = make_float2(-ax[i], -ax[i]);
-            nay[i] = make_float2(-ay[i], -ay[i]);
-            naz[i] = make_float2(-az[i], -az[i]);
-            nbx[i] = make_float2(-bx[i], -bx[i]);
-            nby[i] = make_float2(-by[i], -by[i]);
-            nbz[i] = make_float2(-bz[i], -bz[i]);
-            acco[i] = make_float2(0.f, 0.f);
-            accn[i] = make_float2(0.f, 0.f);
+            px[i] = make_float2(ax[i], bx[i]);
+            py[i] = make_float2(ay[i], by[i]);
+            pz[i] = make_float2(az[i], bz[i]);
+            acc[i] = make_float2(0.f, 0.f);
         }
 #pragma unroll (K == 1 ? 2 : 1)
         for (int c = gtid; c < nv; c += TPW) {
@@ -806,21 +818,46 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
                         Vec<float>::set(Y, e, qnan<float>());
                         Vec<float>::set(Z, e, qnan<float>());
                     }
-            const float2 xa = make_float2(X.x, X.y), xb = make_float2(X.z, X.w);
-            const float2 ya = make_float2(Y.x, Y.y), yb = make_float2(Y.z, Y.w);
-            const float2 za = make_float2(Z.x, Z.y), zb = make_float2(Z.z, Z.w);
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                P.acc5(__fadd2_rn(xa, nax[i]), __fadd2_rn(ya, nay[i]), __fadd2_rn(za, naz[i]), acco[i]);
-                P.acc5(__fadd2_rn(xa, nbx[i]), __fadd2_rn(ya, nby[i]), __fadd2_rn(za, nbz[i]), accn[i]);
-                P.acc5(__fadd2_rn(xb, nax[i]), __fadd2_rn(yb, nay[i]), __fadd2_rn(zb, naz[i]), acco[i]);
-                P.acc5(__fadd2_rn(xb, nbx[i]), __fadd2_rn(yb, nby[i]), __fadd2_rn(zb, nbz[i]), accn[i]);
+            for (int e = 0; e < 4; ++e) {
+                const float xe = Vec<float>::get(X, e), ye = Vec<float>::get(Y, e), ze = Vec<float>::get(Z, e);
+                const float2 xj = make_float2(xe, xe), yj = make_float2(ye, ye), zj = make_float2(ze, ze);
+#pragma unroll
+                for (int i = 0; i < K; ++i)
+                    P.acc5(__ffma2_rn(px[i], P.m1, xj), __ffma2_rn(py[i], P.m1, yj), __ffma2_rn(pz[i], P.m1, zj),
+                           acc[i]);
             }
+        }
+        if constexpr (K > 1) {
+            // the owner of moved atom s_k adds it as a partner of the other moves at a_k and, for
+            // the later moves, writes D_ik = [u(|b_i - b_k|) - u(|a_i - b_k|)] - [u(|b_i - a_k|) - u(|a_i - a_k|)]
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (gtid == cs[k] % TPW) {
+                    const float2 akx = make_float2(ax[k], ax[k]), aky = make_float2(ay[k], ay[k]),
+                                 akz = make_float2(az[k], az[k]);
+                    const float2 bkx = make_float2(bx[k], bx[k]), bky = make_float2(by[k], by[k]),
+                                 bkz = make_float2(bz[k], bz[k]);
+#pragma unroll
+                    for (int i = 0; i < K; ++i) {
+                        if (i == k) continue;
+                        float2 ta = make_float2(0.f, 0.f);
+                        P.acc5(__ffma2_rn(px[i], P.m1, akx), __ffma2_rn(py[i], P.m1, aky),
+                               __ffma2_rn(pz[i], P.m1, akz), ta);
+                        acc[i] = __fadd2_rn(acc[i], ta);
+                        if (i > k) {
+                            float2 tb = make_float2(0.f, 0.f);
+                            P.acc5(__ffma2_rn(px[i], P.m1, bkx), __ffma2_rn(py[i], P.m1, bky),
+                                   __ffma2_rn(pz[i], P.m1, bkz), tb);
+                            dsm[i * K + k] = J.c * ((tb.y - tb.x) - (ta.y - ta.x));
+                        }
+                    }
+                }
         }
         // every partner (the masked ones at the clamp included) is in both sums, so the constants
         // K cancel: S = c (sum_new - sum_old)
 #pragma unroll
-        for (int i = 0; i < K; ++i) S[i] = J.c * ((accn[i].x + accn[i].y) - (acco[i].x + acco[i].y));
+        for (int i = 0; i < K; ++i) S[i] = J.c * (acc[i].y - acc[i].x);
     } else {
 #pragma unroll 2
         for (int c = gtid; c < nv; c += TPW) {
@@ -851,7 +888,7 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
             }
         }
     }
-    if constexpr (K > 1) {
+    if constexpr (K > 1 && !packed5<T, MEXP, SYM>()) {
 #pragma unroll
         for (int k = 0; k < K; ++k)
             if (gtid == cs[k] % TPW) {
