@@ -491,13 +491,13 @@ def run_uneven(args):
     assert torch.all(sw - k0 == SWEEPS_PER_STEP * args.steps), "graph replays must advance the sweep counters"
     pe = sum(2.0 * r[0] * (r[0] - 1) for r in rows) * SWEEPS_PER_STEP
     a_np = acc.cpu().numpy()
-    groups = {}
+    e_by_n = {}
     for r, row in zip(a_np, rows):
-        groups.setdefault(row[0], []).append(r[0] / r[6] / row[0])
+        e_by_n.setdefault(row[0], []).append(r[0] / r[6] / row[0])
     print(json.dumps({"config": "uneven batch, one persistent launch per step, CUDA graph replay",
                       "walkers": W, "threads_per_walker": tpw, "walkers_per_cta": groups, "ms_per_step": ms,
                       "pair_evals_per_s": pe / (ms * 1e-3),
-                      "E_per_atom_by_N": {str(k): float(np.mean(v)) for k, v in sorted(groups.items())}}), flush=True)
+                      "E_per_atom_by_N": {str(k): float(np.mean(v)) for k, v in sorted(e_by_n.items())}}), flush=True)
     return 0
 
 

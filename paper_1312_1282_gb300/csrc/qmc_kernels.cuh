@@ -907,6 +907,27 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
 // 2 phases x K x (TPW/32) slots.
 template <int TPW, int K, typename T> __device__ __forceinline__ void group_sum_k(T (&v)[K], T *red, int ph, int bar_id, int gtid)
 {
+    if constexpr (K == 2 && TPW == 128 && std::is_same<T, float>::value) {
+        // two sums in one butterfly: after the first exchange lanes 0-15 carry the first sum and
+        // lanes 16-31 the second (5 shuffles instead of 10: 20.02 against 20.19 ms per step at
+        // N = 1952, 528 walkers); the four warps' partials of a sum are one 16-byte load
+        const int lane = gtid & 31;
+        const bool lo = lane < 16;
+        float keep = lo ? v[0] : v[1];
+        const float send = lo ? v[1] : v[0];
+        keep += __shfl_xor_sync(FULL, send, 16);
+        keep += __shfl_xor_sync(FULL, keep, 8);
+        keep += __shfl_xor_sync(FULL, keep, 4);
+        keep += __shfl_xor_sync(FULL, keep, 2);
+        keep += __shfl_xor_sync(FULL, keep, 1);
+        float *r = red + ph * 8;  // 32-byte aligned: the slots start on a 16-byte boundary
+        if ((lane & 15) == 0) r[(lane >> 4) * 4 + (gtid >> 5)] = keep;
+        group_sync<TPW>(bar_id);
+        const float4 a = reinterpret_cast<const float4 *>(r)[0], b = reinterpret_cast<const float4 *>(r)[1];
+        v[0] = ((a.x + a.y) + a.z) + a.w;
+        v[1] = ((b.x + b.y) + b.z) + b.w;
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < K; ++i) v[i] = warp_sum(v[i]);
     if (TPW == 32) {
