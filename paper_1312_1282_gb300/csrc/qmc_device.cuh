@@ -114,6 +114,7 @@ template <> struct Fn<float> {
     static __device__ __forceinline__ float rsqrt(float x) { return rsqrt_a(x); }
     static __device__ __forceinline__ float rcp(float x) { return rcp_a(x); }
     static __device__ __forceinline__ float exp(float x) { return ex2_a(x * 1.4426950408889634f); }
+    static __device__ __forceinline__ float exp2(float x) { return ex2_a(x); }
     static __device__ __forceinline__ float log(float x) { return lg2_a(x) * 0.6931471805599453f; }
     // x^(-m) for x > 0
     static __device__ __forceinline__ float powneg(float x, float m) { return ex2_a(-m * lg2_a(x)); }
@@ -123,6 +124,7 @@ template <> struct Fn<double> {
     static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double exp2(double x) { return ::exp2(x); }
     static __device__ __forceinline__ double log(double x) { return ::log(x); }
     static __device__ __forceinline__ double powneg(double x, double m) { return ::pow(x, -m); }
     static __device__ __forceinline__ double rint(double x) { return ::rint(x); }
@@ -214,21 +216,44 @@ template <typename T, int MEXP, bool SYM> struct Jas {
 };
 
 // ----------------------------------------------------------------------------------------------
-// HFD-B(HE) (Aziz II) pair potential, K, from r and q = 1/r (published 1987 constants).
+// HFD-B(HE) (Aziz II) pair potential (published 1987 constants)
 // ----------------------------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ T aziz(T r, T q)
-{
-    const T eps = (T)10.948, rm = (T)2.963, A = (T)1.8443101e5, alpha = (T)10.43329537,
-            beta = (T)-2.27965105, C6 = (T)1.36745214, C8 = (T)0.42123807, C10 = (T)0.17473318,
-            D = (T)1.4826;
-    const T x = r * ((T)1 / rm);
-    const T y = (q * q) * (rm * rm);  // x^-2
-    const T disp = (y * y * y) * fma(fma(C10, y, C8), y, C6);
-    const T rep = A * Fn<T>::exp(x * fma(beta, x, -alpha));
-    const T t = fma(D * rm, q, (T)-1);  // D/x - 1
-    const T F = (x < D) ? Fn<T>::exp(-(t * t)) : (T)1;
-    return eps * fma(-F, disp, rep);
-}
+// Aziz II (HFD-B(HE)) potential in K, r in Angstrom (the paper's Sec. 7 potential), with the
+// constants folded in double and rounded once: with x = r/rm, q = 1/r and A = q^6,
+//   eps C_2k / x^2k = A q^(2k-6) (eps C_2k rm^2k)      (k = 3, 4, 5)
+//   eps A* exp(-alpha x + beta x^2) = 2^(e0 + ea r + eb r^2),  e0 = log2(eps A*),
+// and the damping F(x) = exp(-(D/x - 1)^2) for x < D, i.e. r < D rm, where D/x = D rm q.
+// A* = 1.8443101e5 enters only through e0.
+template <typename T> struct Aziz {
+    T k6, k8, k10, e0, ea, eb, Drm;
+    __device__ __forceinline__ Aziz()
+    {
+        const double eps = 10.948, rm = 2.963, alpha = 10.43329537, beta = -2.27965105,
+                     C6 = 1.36745214, C8 = 0.42123807, C10 = 0.17473318, D = 1.4826, log2e = 1.4426950408889634;
+        const double rm2 = rm * rm, rm6 = rm2 * rm2 * rm2;
+        k6 = (T)(eps * C6 * rm6);
+        k8 = (T)(eps * C8 * rm6 * rm2);
+        k10 = (T)(eps * C10 * rm6 * rm2 * rm2);
+        e0 = (T)20.94531715824703;  // log2(eps As) = log2(2.01914469e6), a literal so it stays an immediate
+        ea = (T)(-alpha * log2e / rm);
+        eb = (T)(beta * log2e / rm2);
+        Drm = (T)(D * rm);
+    }
+    // V from r, r^2, q = 1/r, q^2 and A = q^6
+    __device__ __forceinline__ T operator()(T r, T r2, T q, T q2, T A) const
+    {
+        const T disp = A * fma(fma(k10, q2, k8), q2, k6);
+        const T rep = Fn<T>::exp2(fma(eb, r2, fma(ea, r, e0)));
+        const T t = fma(Drm, q, (T)-1);
+        const T F = r < Drm ? Fn<T>::exp(-(t * t)) : (T)1;
+        return fma(-F, disp, rep);
+    }
+    __device__ __forceinline__ T operator()(T r, T r2, T q) const
+    {
+        const T q2 = q * q;
+        return (*this)(r, r2, q, q2, q2 * q2 * q2);
+    }
+};
 
 // ----------------------------------------------------------------------------------------------
 // Periodic cube

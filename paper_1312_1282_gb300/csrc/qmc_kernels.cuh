@@ -377,6 +377,7 @@ __device__ double group_log_psi(const Jas<T, MEXP, SYM> &J, const T *sx, const T
 // is bit-reproducible).  Diagonal tiles (pairs inside one block) form a last round.
 template <int MEXP, bool SYM> struct TilePair {
     const Jas<float, MEXP, SYM> &J;
+    Aziz<float> AZ;
     float L, iL, hL2, m, mm1;
     __device__ __forceinline__ TilePair(const Jas<float, MEXP, SYM> &j)
         : J(j), L(j.L), iL(1.f / j.L), hL2(j.hL2), m(j.m), mm1(j.m * (j.m + 1.f))
@@ -405,19 +406,16 @@ template <int MEXP, bool SYM> struct TilePair {
         gz = g * dz;
         lap = ok ? fmaf(2.f * u1, q, u2) : 0.f;
         // Aziz II; the damping exp(-(D/x - 1)^2) only matters for x < D: skipped when no lane needs it
-        const float eps = 10.948f, rm = 2.963f, A = 1.8443101e5f, alpha = 10.43329537f, beta = -2.27965105f,
-                    C6 = 1.36745214f, C8 = 0.42123807f, C10 = 0.17473318f, D = 1.4826f;
-        const float x = r * (1.f / rm);
-        const float y = (q * q) * (rm * rm);
-        const float disp = (y * y * y) * fmaf(fmaf(C10, y, C8), y, C6);
-        const float rep = A * Fn<float>::exp(x * fmaf(beta, x, -alpha));
+        const float q2 = q * q, A6 = q2 * q2 * q2;
+        const float disp = A6 * fmaf(fmaf(AZ.k10, q2, AZ.k8), q2, AZ.k6);
+        const float rep = Fn<float>::exp2(fmaf(AZ.eb, r2, fmaf(AZ.ea, r, AZ.e0)));
         float F = 1.f;
-        const bool damp = ok && x < D;
+        const bool damp = ok && r < AZ.Drm;
         if (__any_sync(FULL, damp)) {
-            const float t = fmaf(D * rm, q, -1.f);
+            const float t = fmaf(AZ.Drm, q, -1.f);
             F = damp ? Fn<float>::exp(-(t * t)) : 1.f;
         }
-        v = ok ? eps * fmaf(-F, disp, rep) : 0.f;
+        v = ok ? fmaf(-F, disp, rep) : 0.f;
     }
 };
 
@@ -427,8 +425,8 @@ template <int MEXP, bool SYM> struct TilePair {
 // once per walker: with A = q^6, B = w^6 (q = 1/r, w = 1/(L - r)), u'(r) = 5c (B - A) and
 // u''(r) = 30c (A q + B w), so the drift g (r_i - r_j) is returned over GSCALE = 5c and the
 // Laplacian term u'' + 2u'/r = 10c [q (B + 2A) + 3 B w] over LSCALE = 10c.  The Aziz II
-// potential reuses the powers: eps F C_2k / x^2k = F A (k6 + k8 q^2 + k10 q^4) with the
-// constants rm^2k eps C_2k, and eps A* exp(-alpha x + beta x^2) = 2^(e0 + ea r + eb r^2).
+// potential (the folded constants of Aziz) reuses the powers: its dispersion is
+// F A (k6 + k8 q^2 + k10 q^4) and its repulsion 2^(e0 + ea r + eb r^2).
 template <int MEXP, bool SYM> struct TilePair2 {
     static constexpr bool PACKED = MEXP == 5 && SYM;
     TilePair<MEXP, SYM> P;
@@ -436,10 +434,6 @@ template <int MEXP, bool SYM> struct TilePair2 {
     float2 L2, iL2, nL2, M2, nM2, m1, two2, three2, k6, k8, k10, e0, ea, eb;
     __device__ __forceinline__ TilePair2(const Jas<float, MEXP, SYM> &j) : P(j)
     {
-        // Aziz II (HFD-B(HE)) parameters, folded in double and rounded once
-        const double eps = 10.948, rm = 2.963, A = 1.8443101e5, alpha = 10.43329537, beta = -2.27965105,
-                     C6 = 1.36745214, C8 = 0.42123807, C10 = 0.17473318, log2e = 1.4426950408889634;
-        const double rm2 = rm * rm, rm6 = rm2 * rm2 * rm2;
         GSCALE = PACKED ? 5.f * j.c : 1.f;
         LSCALE = PACKED ? 10.f * j.c : 1.f;
         L2 = make_float2(j.L, j.L);
@@ -450,15 +444,13 @@ template <int MEXP, bool SYM> struct TilePair2 {
         m1 = make_float2(-1.f, -1.f);
         two2 = make_float2(2.f, 2.f);
         three2 = make_float2(3.f, 3.f);
-        const float f6 = (float)(eps * C6 * rm6), f8 = (float)(eps * C8 * rm6 * rm2),
-                    f10 = (float)(eps * C10 * rm6 * rm2 * rm2);
-        const float fe0 = (float)log2(eps * A), fea = (float)(-alpha * log2e / rm), feb = (float)(beta * log2e / rm2);
-        k6 = make_float2(f6, f6);
-        k8 = make_float2(f8, f8);
-        k10 = make_float2(f10, f10);
-        e0 = make_float2(fe0, fe0);
-        ea = make_float2(fea, fea);
-        eb = make_float2(feb, feb);
+        const Aziz<float> &az = P.AZ;  // the folded Aziz II constants, in both lanes
+        k6 = make_float2(az.k6, az.k6);
+        k8 = make_float2(az.k8, az.k8);
+        k10 = make_float2(az.k10, az.k10);
+        e0 = make_float2(az.e0, az.e0);
+        ea = make_float2(az.ea, az.ea);
+        eb = make_float2(az.eb, az.eb);
     }
     __device__ __forceinline__ float2 mi(float2 d) const
     {
@@ -498,7 +490,7 @@ template <int MEXP, bool SYM> struct TilePair2 {
             const float2 ex = __ffma2_rn(eb, r2, __ffma2_rn(ea, r, e0));
             const float2 rep = make_float2(ex2_a(ex.x), ex2_a(ex.y));
             float2 nF = m1;
-            const float Drm = 1.4826f * 2.963f;  // x < D is r < D rm
+            const float Drm = P.AZ.Drm;  // x < D is r < D rm
             const bool d0 = ok0 && r.x < Drm, d1 = ok1 && r.y < Drm;
             if (__any_sync(FULL, d0 || d1)) {
                 const float t0 = fmaf(Drm, q.x, -1.f), t1 = fmaf(Drm, q.y, -1.f);
@@ -639,6 +631,11 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
     using V = typename Vec<T>::type;
     constexpr int VN = Vec<T>::N;
     const T L = J.L, iL = (T)1 / J.L, hL2 = J.hL2, m = J.m, mm1 = J.m * (J.m + (T)1);
+    // exponent 5 with the symmetrised u: the Jastrow terms without their constant factors, which
+    // are applied to the row sums (drift times 5c, Laplacian term times 10c)
+    constexpr bool FOLD = MEXP == 5 && SYM;
+    const double gs = FOLD ? 5.0 * (double)J.c : 1.0, ls = FOLD ? 10.0 * (double)J.c : 1.0;
+    const Aziz<T> AZ;
     const int lane = gtid & 31;
     double sV = 0.0, sLap = 0.0, sF2 = 0.0;
     for (int i0 = part * TPW + gtid - lane; i0 < n; i0 += parts * TPW) {  // warp-uniform; this CTA's rows
@@ -665,22 +662,37 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
                     const bool ok = (r2 < hL2) && (j != i) && (j < n);
                     const T q = Fn<T>::rsqrt(r2);
                     const T r = r2 * q;
-                    const T f0 = J.fq(q, r);  // f(r) = c r^-m
-                    T u1 = -m * f0 * q, u2 = mm1 * f0 * (q * q);
-                    if (SYM) {
-                        const T w = L - r, iw = Fn<T>::rcp(w);
-                        const T g0 = J.fq(iw, w);  // f(L - r)
-                        u1 += m * g0 * iw;
-                        u2 += mm1 * g0 * (iw * iw);
-                    }
-                    const T g = u1 * q;
-                    fx += ok ? g * dx : (T)0;
-                    fy += ok ? g * dy : (T)0;
-                    fz += ok ? g * dz : (T)0;
-                    if (upper) {
-                        const bool half = ok && j > i;
-                        lap += half ? fma((T)2 * u1, q, u2) : (T)0;
-                        v += half ? aziz(r, q) : (T)0;
+                    if constexpr (FOLD) {
+                        // A = q^6, B = w^6: u'/r = 5c (B - A) q, u'' + 2u'/r = 10c [q (B + 2A) + 3 B w]
+                        const T q2 = q * q, A6 = q2 * q2 * q2;
+                        const T iw = Fn<T>::rcp(L - r), w2 = iw * iw, B6 = w2 * w2 * w2;
+                        const T g = (B6 - A6) * q;
+                        fx += ok ? g * dx : (T)0;
+                        fy += ok ? g * dy : (T)0;
+                        fz += ok ? g * dz : (T)0;
+                        if (upper) {
+                            const bool half = ok && j > i;
+                            lap += half ? fma(fma((T)2, A6, B6), q, B6 * ((T)3 * iw)) : (T)0;
+                            v += half ? AZ(r, r2, q, q2, A6) : (T)0;
+                        }
+                    } else {
+                        const T f0 = J.fq(q, r);  // f(r) = c r^-m
+                        T u1 = -m * f0 * q, u2 = mm1 * f0 * (q * q);
+                        if (SYM) {
+                            const T w = L - r, iw = Fn<T>::rcp(w);
+                            const T g0 = J.fq(iw, w);  // f(L - r)
+                            u1 += m * g0 * iw;
+                            u2 += mm1 * g0 * (iw * iw);
+                        }
+                        const T g = u1 * q;
+                        fx += ok ? g * dx : (T)0;
+                        fy += ok ? g * dy : (T)0;
+                        fz += ok ? g * dz : (T)0;
+                        if (upper) {
+                            const bool half = ok && j > i;
+                            lap += half ? fma((T)2 * u1, q, u2) : (T)0;
+                            v += half ? AZ(r, r2, q) : (T)0;
+                        }
                     }
                 }
             }
@@ -691,9 +703,9 @@ __device__ void group_energy(const Jas<T, MEXP, SYM> &J, const T *sx, const T *s
             sfz.add(fz);
         }
         if (row) {
-            const double fx = sfx.value(), fy = sfy.value(), fz = sfz.value();
+            const double fx = gs * sfx.value(), fy = gs * sfy.value(), fz = gs * sfz.value();
             sV += sv.value();
-            sLap += 2.0 * slap.value();  // each pair's Laplacian term belongs to both atoms
+            sLap += 2.0 * ls * slap.value();  // each pair's Laplacian term belongs to both atoms
             sF2 += fx * fx + fy * fy + fz * fz;
         }
     }
@@ -1634,6 +1646,7 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
     // m-derivative of the shift 2 f(L/2): 2 f(L/2) ln(2b/L)
     const T Km = (T)(d.K * ::log(d.b > 0 ? 2.0 * d.b / d.L : 1.0));
     const T c1 = (T)1 / m, c2 = (T)(2.0 * d.m + 1.0) / (m * (m + (T)1));
+    const Aziz<T> AZ;
     double sLp = 0, sLpm = 0, sV = 0, sLap = 0, sLapm = 0, sF2 = 0, sFFm = 0;
     for (int i = part * TPW + gtid; i < n; i += a.parts * TPW) {  // this CTA's share of the rows
         const T xi = sx[i], yi = sy[i], zi = sz[i];
@@ -1670,7 +1683,7 @@ __global__ void __launch_bounds__(TPW) grad_kernel(PassArgs a)
                         u1m -= g1 * (c1 + lbw);
                         u2m += g2 * (c2 + lbw);
                     }
-                    const T vv = aziz(r, q);
+                    const T vv = AZ(r, r2, q);
                     lp += ok ? uu : (T)0;
                     lpm += ok ? um : (T)0;
                     v += ok ? vv : (T)0;
