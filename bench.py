@@ -235,8 +235,11 @@ def run_native(args):
     torch.cuda.synchronize()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    # measured arithmetic rates of this GPU (per second per SM), outside the timed region
-    probe = q.qmc_probe_rates(4, 256, 2000)
+    # measured arithmetic rates of this GPU (per second per SM), outside the timed region, in the
+    # sweep's own shape: its CTA size and its resident CTAs per SM at 128 registers per thread
+    probe_thr = min(512, tpw * groups)
+    probe_bps = max(1, 65536 // (128 * probe_thr))
+    probe = q.qmc_probe_rates(probe_bps, probe_thr, 2000)
 
     def one_step():
         q.qmc_sweep(d, opt, pos, logpsi, sweeps, seed, SWEEPS_PER_STEP, SWEEPS_PER_STEP, accum, stream)
@@ -405,9 +408,11 @@ def run_native(args):
                             "achieved_tops": energy_ops, "frac": energy_ops / peak_tops,
                             "how": "step time minus the median of 3 steps without the energy sample"},
             "probe": {"per_clock_per_sm": {k: v / (clk * 1e6) for k, v in probe.items()},
-                      "how": "qmc_probe_rates(4 CTAs/SM, 256 threads, 2000 iters), CUDA events; per clock at the "
-                             "run's maximum SM clock",
+                      "how": f"qmc_probe_rates({probe_bps} CTAs/SM, {probe_thr} threads, 2000 iters), the sweep's "
+                             "shape; CUDA events; per clock at the run's maximum SM clock",
                       "pair_evals_per_clock_per_sm_achieved": value / world / (nsm * clk * 1e6),
+                      "pair_evals_per_clock_per_sm_move_phase": pe_step / ((total_ms / args.steps - energy_ms) * 1e-3)
+                      / (nsm * clk * 1e6),
                       "pair_evals_per_clock_per_sm_of_probe": probe["pair_evals"] / (clk * 1e6),
                       "ffma_measured_tops": probe["ffma"] * nsm / 1e12,
                       "frac_of_measured_ffma": achieved / (probe["ffma"] * nsm / 1e12)},
