@@ -113,14 +113,16 @@ __device__ __forceinline__ void cluster_sync_all()
 
 // Moves per exchange.  A batch of CLUSTER_KB consecutive moves of distinct atoms is evaluated
 // against the configuration at the start of the batch, as in the one-CTA batched moves: every CTA
-// sums the partner terms of all the batch's moves over its slice (the batch's atoms masked), one
-// exchange carries the CLUSTER_KB partial sums, and the decisions are taken in order with the
-// moved atoms' own terms and the cross terms D_ik, which every warp computes (one pair per lane).
-// One cluster round trip per batch instead of one per move.
-// Measured with 13 walkers of N = 40 960: 85.2 ms per macroupdate with 4 moves per exchange,
-// 88.4 ms with 8 (two passes of 4 over the slice and two rounds of cross terms), 131 ms with 1.
+// sums the partner terms of all the batch's moves over its slice in one pass (the batch's atoms
+// masked), one exchange carries the CLUSTER_KB partial sums, and the decisions are taken in order
+// with the moved atoms' own terms and the cross terms D_ik, which every warp computes (one pair
+// per lane).  One cluster round trip per batch instead of one per move.
+// Measured with 13 walkers of N = 40 960 (alternating runs on one GB300), ms per macroupdate:
+// each move's (old, new) position in one f32x2, 8 moves per exchange 84.4, 4 moves 87.4; two
+// partners per f32x2 (eight registers more per move), 4 moves 87.7, 8 moves in two passes over
+// the slice 88.4; one move per exchange 131.
 #ifndef QMC_CLUSTER_KB
-#define QMC_CLUSTER_KB 4
+#define QMC_CLUSTER_KB 8
 #endif
 constexpr int CLUSTER_KB = QMC_CLUSTER_KB;
 static_assert(CLUSTER_KB == 1 || CLUSTER_KB == 2 || CLUSTER_KB == 4 || CLUSTER_KB == 8,
@@ -283,26 +285,17 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
             bz[i] = wrap(az[i] + __shfl_sync(FULL, mdz, tt + i), L);
             cs[i] = own[i] == (int)rank ? ls[i] >> 2 : -1;
         }
-        // partner terms over this slice, the batch's atoms masked (they add zero); at most four
-        // moves per pass over the slice (their accumulators fill the registers), so a batch of
-        // eight moves reads the slice twice before its one exchange
-        constexpr int SUB = KK < 4 ? KK : 4;
+        // partner terms over this slice, the batch's atoms masked (they add zero): each move holds
+        // its old and new position in one f32x2 and every partner is duplicated into both lanes
         float v[K];
+        {
+            float2 px[KK], py[KK], pz[KK], acc2[KK];
 #pragma unroll
-        for (int i = 0; i < K; ++i) v[i] = 0.f;
-#pragma unroll
-        for (int q0 = 0; q0 < KK; q0 += SUB) {
-            float2 nax[SUB], nay[SUB], naz[SUB], nbx[SUB], nby[SUB], nbz[SUB], acco[SUB], accn[SUB];
-#pragma unroll
-            for (int i = 0; i < SUB; ++i) {
-                nax[i] = make_float2(-ax[q0 + i], -ax[q0 + i]);
-                nay[i] = make_float2(-ay[q0 + i], -ay[q0 + i]);
-                naz[i] = make_float2(-az[q0 + i], -az[q0 + i]);
-                nbx[i] = make_float2(-bx[q0 + i], -bx[q0 + i]);
-                nby[i] = make_float2(-by[q0 + i], -by[q0 + i]);
-                nbz[i] = make_float2(-bz[q0 + i], -bz[q0 + i]);
-                acco[i] = make_float2(0.f, 0.f);
-                accn[i] = make_float2(0.f, 0.f);
+            for (int i = 0; i < KK; ++i) {
+                px[i] = make_float2(ax[i], bx[i]);
+                py[i] = make_float2(ay[i], by[i]);
+                pz[i] = make_float2(az[i], bz[i]);
+                acc2[i] = make_float2(0.f, 0.f);
             }
             for (int c = gtid; c < nv; c += TPW) {
                 float4 X = reinterpret_cast<const float4 *>(sx)[c];
@@ -316,19 +309,18 @@ __global__ void __launch_bounds__(TPW, 1) sweep_cluster_kernel(ClusterArgs a)
                         Vec<float>::set(Y, e, qnan<float>());
                         Vec<float>::set(Z, e, qnan<float>());
                     }
-                const float2 xa = make_float2(X.x, X.y), xb = make_float2(X.z, X.w);
-                const float2 ya = make_float2(Y.x, Y.y), yb = make_float2(Y.z, Y.w);
-                const float2 za = make_float2(Z.x, Z.y), zb = make_float2(Z.z, Z.w);
 #pragma unroll
-                for (int i = 0; i < SUB; ++i) {
-                    P.acc5(__fadd2_rn(xa, nax[i]), __fadd2_rn(ya, nay[i]), __fadd2_rn(za, naz[i]), acco[i]);
-                    P.acc5(__fadd2_rn(xa, nbx[i]), __fadd2_rn(ya, nby[i]), __fadd2_rn(za, nbz[i]), accn[i]);
-                    P.acc5(__fadd2_rn(xb, nax[i]), __fadd2_rn(yb, nay[i]), __fadd2_rn(zb, naz[i]), acco[i]);
-                    P.acc5(__fadd2_rn(xb, nbx[i]), __fadd2_rn(yb, nby[i]), __fadd2_rn(zb, nbz[i]), accn[i]);
+                for (int e = 0; e < 4; ++e) {
+                    const float xe = Vec<float>::get(X, e), ye = Vec<float>::get(Y, e), ze = Vec<float>::get(Z, e);
+                    const float2 xj = make_float2(xe, xe), yj = make_float2(ye, ye), zj = make_float2(ze, ze);
+#pragma unroll
+                    for (int i = 0; i < KK; ++i)
+                        P.acc5(__ffma2_rn(px[i], P.m1, xj), __ffma2_rn(py[i], P.m1, yj), __ffma2_rn(pz[i], P.m1, zj),
+                               acc2[i]);
                 }
             }
 #pragma unroll
-            for (int i = 0; i < SUB; ++i) v[q0 + i] = J.c * ((accn[i].x + accn[i].y) - (acco[i].x + acco[i].y));
+            for (int i = 0; i < K; ++i) v[i] = i < KK ? J.c * (acc2[i].y - acc2[i].x) : 0.f;
         }
         // The batch's atoms as partners of its other moves: pair p = lane + 32 r (round r) stands
         // for move i = p / KK and atom k = p % KK; for k != i it holds
