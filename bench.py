@@ -218,6 +218,8 @@ def run_native(args):
     pos = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
     logpsi = torch.zeros(W, dtype=torch.float64, device="cuda")
     sweeps = torch.zeros(W, dtype=torch.int64, device="cuda")
+    if args.stagger:  # walker w starts at sweep w mod 5: its energy samples fall on other sweeps
+        sweeps += torch.arange(W, device="cuda") % SWEEPS_PER_STEP
     accum = torch.zeros(W, q.NACC, dtype=torch.float64, device="cuda")
     q.qmc_init_walkers(batch_descs(0.8), seed, 0.1, opt, pos)
     q.qmc_log_psi(batch_descs(0.8), opt, pos, logpsi)
@@ -391,7 +393,7 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_atoms": n, "walkers_per_gpu": W, "sweeps_per_step": SWEEPS_PER_STEP,
                        "energy_every": SWEEPS_PER_STEP, "step_A": round(step, 4), "threads_per_walker": tpw,
-                       "walkers_per_cta": groups,
+                       "walkers_per_cta": groups, "sweep_phase": "staggered" if args.stagger else "aligned",
                        "sms": nsm, "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas{world}"},
             "sweeps_per_s": sweeps_per_s,
             "energy_pairs_per_s": energy_pairs * world * args.steps / (total_ms * 1e-3),
@@ -948,6 +950,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--tpw", type=int, default=0, help="threads per walker of the headline run (0: autotune)")
     ap.add_argument("--groups", type=int, default=0, help="walkers per CTA with --tpw (default 1)")
+    ap.add_argument("--stagger", action="store_true", help="start walker w at sweep w mod 5")
     ap.add_argument("--large-n", type=int, default=10000, help="large: atoms per walker")
     ap.add_argument("--c3-pair-sweeps", type=int, default=600, help="c3: paired FP32/FP64 sweeps")
     ap.add_argument("--c3-pair-equil", type=int, default=20, help="c3: FP64 relaxation sweeps before pairing")

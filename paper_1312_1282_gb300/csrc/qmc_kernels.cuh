@@ -915,8 +915,10 @@ __device__ __forceinline__ void batch_partners(const Jas<T, MEXP, SYM> &J, const
     }
 }
 
-// Sum K values over the group with one barrier (identical in every thread).  red holds
-// 2 phases x K x (TPW/32) slots.
+// Sum K <= KB values over the group with one barrier (identical in every thread).  red holds
+// 2 phases x KB x (TPW/32) slots.  The phases are KB x (TPW/32) slots apart for every K, so that a
+// batch of K moves and a following single move (ph alternates) never share a slot: a thread that
+// is already writing the next batch's partials cannot overwrite ones another thread still reads.
 template <int TPW, int K, typename T> __device__ __forceinline__ void group_sum_k(T (&v)[K], T *red, int ph, int bar_id, int gtid)
 {
     if constexpr (K == 2 && TPW == 128 && std::is_same<T, float>::value) {
@@ -932,7 +934,7 @@ template <int TPW, int K, typename T> __device__ __forceinline__ void group_sum_
         keep += __shfl_xor_sync(FULL, keep, 4);
         keep += __shfl_xor_sync(FULL, keep, 2);
         keep += __shfl_xor_sync(FULL, keep, 1);
-        float *r = red + ph * 8;  // 32-byte aligned: the slots start on a 16-byte boundary
+        float *r = red + ph * (KB * 4);  // 16-byte aligned: the slots start on a 16-byte boundary
         if ((lane & 15) == 0) r[(lane >> 4) * 4 + (gtid >> 5)] = keep;
         group_sync<TPW>(bar_id);
         const float4 a = reinterpret_cast<const float4 *>(r)[0], b = reinterpret_cast<const float4 *>(r)[1];
@@ -947,7 +949,7 @@ template <int TPW, int K, typename T> __device__ __forceinline__ void group_sum_
         return;
     }
     constexpr int NW = TPW / 32;
-    T *r = red + ph * K * NW;
+    T *r = red + ph * KB * NW;  // phases KB x NW apart whatever K: batches of any size alternate safely
     if ((gtid & 31) == 0) {
 #pragma unroll
         for (int i = 0; i < K; ++i) r[i * NW + (gtid >> 5)] = v[i];
