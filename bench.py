@@ -253,6 +253,7 @@ def run_native(args):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(_bus_id(torch, dev))
+    sweeps_before = sweeps.cpu().numpy().astype(np.int64)
     launches0 = q.qmc_launch_count()
     if dist:
         dist.barrier()
@@ -276,6 +277,16 @@ def run_native(args):
         total_ms = t.item()
         dist.barrier()
     stats = replicas.block_stats(accum, n)
+    # ln psi drift over the timed steps: at every recompute (after sweeps k with (k+1) % 50 == 0)
+    # the kernel adds |ln psi carried - ln psi recomputed| to field 8 and keeps the maximum in 9
+    acc_host = accum.cpu().numpy()
+    sweeps_after = sweeps.cpu().numpy().astype(np.int64)
+    recomputes = int((sweeps_after // 50 - sweeps_before // 50).sum())
+    drift = {"max": float(acc_host[:, 9].max()),
+             "mean": float(acc_host[:, 8].sum()) / recomputes if recomputes else None,
+             "recomputes": recomputes, "every_sweeps": 50,
+             "relative_max": float((acc_host[:, 9] / np.abs(logpsi.cpu().numpy())).max()),
+             "how": "|ln psi carried (FP32 sum of the accepted Delta) - ln psi recomputed| at each recompute"}
 
     # ---- the energy pass on its own: the same step without the energy sample (untimed by the
     # bench line; the chains advance as in any step) ----
@@ -406,6 +417,7 @@ def run_native(args):
             "e2e": {"value": pe_step * world / (e2e_ms * 1e-3), "unit": "pair evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "copy_ms_per_step": copy_ms},
             "gpu_launches": launches,
+            "lnpsi_drift": drift,
             "energy_pass": {"ms_per_sample": energy_ms, "pairs_per_s": energy_pairs * world / (energy_ms * 1e-3),
                             "achieved_tops": energy_ops, "frac": energy_ops / peak_tops,
                             "how": "step time minus the median of 3 steps without the energy sample"},
