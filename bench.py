@@ -105,6 +105,13 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def recomputes_between(before, after, every):
+    """Number of ln psi recomputes while a walker's sweep counter goes from `before` to `after`:
+    the sweeps k in [before, after) with (k + 1) % every == 0, i.e. the multiples of `every` in
+    (before, after]."""
+    return after // every - before // every
+
+
 def _bus_id(torch, dev):
     try:
         p = torch.cuda.get_device_properties(dev)
@@ -281,7 +288,7 @@ def run_native(args):
     # the kernel adds |ln psi carried - ln psi recomputed| to field 8 and keeps the maximum in 9
     acc_host = accum.cpu().numpy()
     sweeps_after = sweeps.cpu().numpy().astype(np.int64)
-    recomputes = int((sweeps_after // 50 - sweeps_before // 50).sum())
+    recomputes = int(recomputes_between(sweeps_before, sweeps_after, 50).sum())
     drift = {"max": float(acc_host[:, 9].max()),
              "mean": float(acc_host[:, 8].sum()) / recomputes if recomputes else None,
              "recomputes": recomputes, "every_sweeps": 50,

@@ -26,3 +26,17 @@ def test_warmup_below_three_is_rejected():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--warmup", "2"],
                        cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert r.returncode != 0
+
+
+def test_recompute_count_matches_the_sweep_rule():
+    """The benchmark line's ln psi drift is averaged over the recomputes of the timed steps; the
+    count must match the sweep's rule (a recompute after sweep k when (k + 1) % every == 0)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(7)
+    for every in (1, 5, 50):
+        before = rng.integers(0, 400, size=200)
+        after = before + rng.integers(0, 300, size=200)
+        brute = [sum((k + 1) % every == 0 for k in range(b, a)) for b, a in zip(before, after)]
+        assert list(bench.recomputes_between(before, after, every)) == brute
