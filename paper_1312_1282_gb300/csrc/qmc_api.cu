@@ -82,6 +82,7 @@ struct Plan {
     size_t part_cap = 0;
     int maxn = 0, maxpad = 0, maxsites = 0;
     bool m5 = true;
+    bool gauss_ok = false;  // descriptors validated for the Gaussian proposal's longer reach
 };
 
 struct Tuned {
@@ -330,6 +331,14 @@ int get_plan(const qmc_walker_desc *d, int W, const qmc_options *o, cudaStream_t
         Plan *p = *it;
         if (p->key == key && p->W == W && p->device == dev && p->sym == sym &&
             std::memcmp(p->descs.data(), d, sizeof(qmc_walker_desc) * (size_t)W) == 0) {
+            // the step check depends on the proposal: a batch registered by a cube-proposal call
+            // is checked again, once, for the Gaussian proposal's reach
+            if (o->proposal == QMC_GAUSS && !p->gauss_ok) {
+                DevWalker tmp;
+                for (int w = 0; w < W; ++w)
+                    if ((rc = resolve_one(d[w], w, o, tmp))) return rc;
+                p->gauss_ok = true;
+            }
             g_plans.splice(g_plans.begin(), g_plans, it);
             out = p;
             return QMC_OK;
@@ -344,6 +353,7 @@ int get_plan(const qmc_walker_desc *d, int W, const qmc_options *o, cudaStream_t
     p->key = key;
     p->W = W;
     p->sym = sym;
+    p->gauss_ok = o->proposal == QMC_GAUSS;
     p->descs.assign(d, d + W);
     std::vector<DevWalker> host;
     std::vector<int> order;

@@ -155,6 +155,26 @@ def test_capacity_and_argument_errors():
             q.qmc_local_energy(q.descs([bad]), q.options(), big.pos, zeros(5))
 
 
+def test_gaussian_step_is_checked_on_a_batch_registered_by_a_cube_call():
+    """The step check depends on the proposal: a Gaussian displacement reaches about 6.8 sigma,
+    a cube one its half-width.  A batch first registered by a cube-proposal call (which caches its
+    walker table) must still refuse a Gaussian call whose reach is a box side or more, before
+    anything is enqueued, and must keep working for the cube proposal."""
+    n = 64
+    L = qi.box_side(n, qi.RHO_HE)  # 14.3 A: a 3 A step is fine for the cube, 6.8 x 3 A is not
+    P = lattice_batch([n], q.QMC_FP32, seed=90, steps=3.0)
+    lp, sw, acc = zeros(1), zeros(1, torch.int64), zeros((1, q.NACC))
+    q.qmc_sweep(P.d, q.options(), P.pos, lp, sw, 5, 1, 0, acc)
+    assert q.qmc_status(timeout_ms=60000) == 0
+    before = P.pos.clone()
+    with pytest.raises(q.QmcError, match="ARG.*step too large"):
+        q.qmc_sweep(P.d, q.options(proposal=q.QMC_GAUSS), P.pos, lp, sw, 5, 1, 0, acc)
+    assert torch.equal(P.pos, before) and sw.cpu().tolist() == [1]
+    q.qmc_sweep(P.d, q.options(), P.pos, lp, sw, 5, 1, 0, acc)
+    assert q.qmc_status(timeout_ms=60000) == 0 and sw.cpu().tolist() == [2]
+    assert 3.0 < L < 6.8 * 3.0
+
+
 def test_nonfinite_coordinates_are_flagged_not_faulted():
     P = lattice_batch([64, 64], q.QMC_FP32, seed=60)
     before = P.pos.clone()
