@@ -55,8 +55,6 @@ int cuda_fail(cudaError_t e, const char *what)
 struct DeviceState {
     unsigned *err = nullptr;
     int nsm = 0;
-    float *fscr = nullptr;  // drift arrays of the tiled energy pass kept in global memory
-    size_t fscr_bytes = 0;
 };
 
 std::mutex g_mu;
@@ -80,6 +78,8 @@ struct Plan {
     double *part_out = nullptr;  // shares of split passes: W x parts x 8 doubles (grown on demand)
     unsigned *part_ctr = nullptr;  // [W] finished parts per walker, zero between launches
     size_t part_cap = 0;
+    float *fscr = nullptr;  // drift arrays of the tiled energy pass kept in global memory, per
+    size_t fscr_bytes = 0;  // batch, so that sweeps of different batches may overlap
     int maxn = 0, maxpad = 0, maxsites = 0;
     bool m5 = true;
     bool gauss_ok = false;  // descriptors validated for the Gaussian proposal's longer reach
@@ -310,6 +310,7 @@ void free_plan(Plan *p)
     if (p->q_ctr) cudaFree(p->q_ctr);
     if (p->part_out) cudaFree(p->part_out);
     if (p->part_ctr) cudaFree(p->part_ctr);
+    if (p->fscr) cudaFree(p->fscr);
     delete p;
 }
 
@@ -420,19 +421,19 @@ int choose_tpw(const Plan &P, const qmc_options *o, int dev, int nsm)
     return std::max(32, std::min(t, 1024));
 }
 
-// the library-owned drift scratch of the tiled energy pass, at least `need` bytes (not under capture)
-int drift_scratch(DeviceState *ds, size_t need, float **out)
+// the batch's drift scratch of the tiled energy pass, at least `need` bytes (not under capture)
+int drift_scratch(Plan &P, size_t need, float **out)
 {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (ds->fscr_bytes < need) {
-        if (ds->fscr) cudaFree(ds->fscr);
-        ds->fscr = nullptr;
-        ds->fscr_bytes = 0;
-        cudaError_t e = cudaMalloc(&ds->fscr, need);
+    if (P.fscr_bytes < need) {
+        if (P.fscr) cudaFree(P.fscr);
+        P.fscr = nullptr;
+        P.fscr_bytes = 0;
+        cudaError_t e = cudaMalloc(&P.fscr, need);
         if (e != cudaSuccess) return cuda_fail(e, "drift scratch");
-        ds->fscr_bytes = need;
+        P.fscr_bytes = need;
     }
-    *out = ds->fscr;
+    *out = P.fscr;
     return QMC_OK;
 }
 
@@ -613,7 +614,7 @@ int mixed_sweep(const qmc_walker_desc *d, int W, const qmc_options *o, const Pla
     const size_t fs = tile_s == 2 ? (size_t)grid * Gs * 3 * small.stride : 0;
     if (fb + fs > 0) {
         float *f = nullptr;
-        int rc = drift_scratch(p.ds, (fb + fs) * sizeof(float), &f);
+        int rc = drift_scratch(*p.plan, (fb + fs) * sizeof(float), &f);
         if (rc) return rc;
         if (fb) big.fscr = f;
         if (fs) small.fscr = f + fb;
@@ -799,7 +800,7 @@ int sweep_impl(const qmc_walker_desc *d, int W, const qmc_options *o, void *pos,
     }
     a.fscr = nullptr;
     if (a.tile == 2) {  // drift scratch of every resident group, grown on demand (not under capture)
-        if ((rc = drift_scratch(p.ds, (size_t)grid * G * 3 * sh.stride * sizeof(float), &a.fscr))) return rc;
+        if ((rc = drift_scratch(*p.plan, (size_t)grid * G * 3 * sh.stride * sizeof(float), &a.fscr))) return rc;
     }
     e = launch_sweep(o->precision, tpw, v, grid, G * tpw, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
@@ -1154,10 +1155,7 @@ void qmc_shutdown(void)
     g_tuned.clear();
     for (auto &ds : g_dev) {
         if (ds.err) cudaFree(ds.err);
-        if (ds.fscr) cudaFree(ds.fscr);
         ds.err = nullptr;
-        ds.fscr = nullptr;
-        ds.fscr_bytes = 0;
         ds.nsm = 0;
     }
 }

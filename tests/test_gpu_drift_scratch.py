@@ -52,3 +52,40 @@ def test_sweep_energy_with_drift_scratch_matches_the_pass():
     en = e.cpu().numpy()
     for w in range(W):
         assert np.all(np.abs(a[w, [2, 3, 4, 5, 0]] - en[w]) <= 1e-5 * energy_scale(en[w])), w
+
+
+def test_batches_on_two_streams_keep_their_own_drift_scratch():
+    """Sweeps of two different batches may run at the same time on two streams.  Each batch's
+    energy samples use that batch's own drift scratch, so overlapping calls give bit for bit
+    the chains and sums of calls made one after the other."""
+    n, W = 3000, 8  # 3000 atoms at 128 threads per walker select the scratch; 16 CTAs run together
+    L = qi.box_side(n, qi.RHO_HE)
+    pad = qi.pad4(n)
+    opt = q.options(precision=q.QMC_FP32, recompute_every=0, threads_per_walker=128)
+    batches = [q.descs([(n, pad, w * 3 * pad, first + w, L, 0.0, qi.B_HE, 5.0, 0.8) for w in range(W)])
+               for first in (0, W)]
+    starts = []
+    for d in batches:
+        p = torch.empty(W * 3 * pad, dtype=torch.float32, device="cuda")
+        q.qmc_init_walkers(d, 21, 0.1, opt, p)
+        starts.append(p)
+
+    def state():
+        return [(p.clone(), zeros(W), zeros(W, torch.int64), zeros((W, q.NACC))) for p in starts]
+
+    one_after_other = state()
+    for d, (p, lp, sw, acc) in zip(batches, one_after_other):
+        q.qmc_sweep(d, opt, p, lp, sw, 21, 2, 1, acc)
+    assert q.qmc_status(timeout_ms=300000) == 0
+
+    together = state()
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for d, (p, lp, sw, acc), st in zip(batches, together, streams):
+        q.qmc_sweep(d, opt, p, lp, sw, 21, 2, 1, acc, st)
+    torch.cuda.synchronize()
+    assert q.qmc_status(timeout_ms=300000) == 0
+    for a, b in zip(one_after_other, together):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    assert np.all(one_after_other[0][3].cpu().numpy()[:, 6] == 2)  # two energy samples per walker
